@@ -1,0 +1,220 @@
+/*
+ * lflts.h -- C ABI of the GB300 library for MLMC with stabilised leapfrog
+ * local time-stepping (LF-LTS) of the mass-lumped P1 wave equation.
+ *
+ * Method: Grote, Michel, Nobile, "Uncertainty quantification by MLMC and
+ * local time-stepping for wave propagation" (arXiv 2106.11117).
+ *   - model problem u_tt - div(c^2(x,w) grad u) = 0, u(0) = u0, u_t(0) = v0,
+ *     homogeneous Dirichlet boundary (Sec. 2.1, Eq. Wave_hd);
+ *   - P1 elements, lumped mass M, stiffness K(w) (Sec. 3.1);
+ *   - stabilised LF-LTS with the diagonal 0/1 mask P, ratio p and
+ *     stabilisation nu (Sec. 3.3, Alg. 2), leapfrog when p = 1 or P = 0
+ *     (Eq. LF2scheme);
+ *   - QoI Q(w) = sum_k g_k u_h(x_k, T, w), a linear functional (Sec. 2.1);
+ *   - MLMC level sums for the estimator and variance (Sec. 2.2, Eqs.
+ *     MLMCestimator and Vell_est); fine/coarse pairs share one draw.
+ *
+ * Conventions
+ *   - Every call returns an lflts_status (0 = success, < 0 = error).  On error
+ *     lflts_last_error(ctx) returns a message owned by the context, valid
+ *     until the next call on that context.
+ *   - Host arrays passed in are owned by the caller and copied before the
+ *     call returns.  Device arrays are owned by the caller.
+ *   - mem = LFLTS_MEM_HOST: xi and outputs are host pointers; the call copies
+ *     xi to the device, runs on `stream` and synchronises the stream before
+ *     returning.  mem = LFLTS_MEM_DEVICE: xi and outputs are device pointers of
+ *     the context's device; the call only enqueues work on `stream` and
+ *     returns (outputs are ready when the stream reaches that point).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - A context belongs to one host thread at a time; it owns all device
+ *     memory it allocates (meshes, fields, workspaces) and frees it in
+ *     lflts_destroy.
+ *   - Random coefficients: the field is c_e^2 = exp(sum_k xi_k psi[e][k]) on
+ *     each triangle e (the random field evaluated at one quadrature point per
+ *     element).  xi is row-major [S][K] FP64, one row per sample.
+ */
+#ifndef LFLTS_H
+#define LFLTS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lflts_ctx lflts_ctx;
+
+typedef enum {
+  LFLTS_OK = 0,
+  LFLTS_ERR_ARG = -1,      /* invalid argument (sizes, ids, pointers)          */
+  LFLTS_ERR_OOM = -2,      /* device or host allocation failed                 */
+  LFLTS_ERR_CUDA = -3,     /* a CUDA runtime call failed (message has details) */
+  LFLTS_ERR_UNSTABLE = -4, /* a sample produced a non-finite QoI               */
+  LFLTS_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up               */
+  LFLTS_ERR_MESH = -6      /* invalid mesh (index range, orientation, masks)   */
+} lflts_status;
+
+enum { LFLTS_MEM_HOST = 0, LFLTS_MEM_DEVICE = 1 };
+
+/* Kernel classes for lflts_profile_read (timing and algorithmic bytes). */
+enum {
+  LFLTS_KERNEL_INIT = 0,   /* state initialisation from u0, v0              */
+  LFLTS_KERNEL_COARSE = 1, /* w-part: full apply M^-1 K u_n + update off R  */
+  LFLTS_KERNEL_INNER = 2,  /* one inner LTS substep on R (Alg. 2 loop)      */
+  LFLTS_KERNEL_QOI = 3,    /* QoI reduction (both stages)                   */
+  LFLTS_KERNEL_SUMS = 4,   /* MLMC level sums                               */
+  LFLTS_KERNEL_CLASSES = 5
+};
+
+/* Library version (major*10000 + minor*100 + patch). */
+int lflts_version(void);
+
+/* Create a context on CUDA device `device` (or -1: a host-only context that
+ * can prepare meshes but not solve).  *out receives the handle. */
+int lflts_create(lflts_ctx** out, int device);
+
+/* Free every device buffer and stream of the context, then the context. */
+int lflts_destroy(lflts_ctx* ctx);
+
+/* Last error message of the context (never NULL; "" after success). */
+const char* lflts_last_error(const lflts_ctx* ctx);
+
+/*
+ * Register a P1 triangle mesh with its LTS mask and random-field basis
+ * (Sec. 3.1 discretisation; Sec. 3.3 mask P).
+ *   xy        [n_nodes][2] FP64 node coordinates
+ *   tri       [n_tri][3] int32 vertex indices, counter-clockwise
+ *   dirichlet [n_nodes] 0/1, 1 = homogeneous Dirichlet node (u = 0)
+ *   P         [n_nodes] 0/1, the diagonal of P (refined region and the
+ *             elements adjacent to it); entries on Dirichlet nodes ignored;
+ *             may be NULL (P = 0, plain leapfrog)
+ *   psi       [n_tri][K] FP64 field basis at the element quadrature point
+ *   K         number of field terms, 1 <= K <= 16
+ * The library reorders the nodes internally; every nodal array crossing the
+ * ABI uses the caller's node order.  Errors: LFLTS_ERR_MESH for indices out
+ * of range or a triangle with non-positive signed area.
+ */
+int lflts_mesh_add(lflts_ctx* ctx, const double* xy, int64_t n_nodes,
+                   const int32_t* tri, int64_t n_tri, const uint8_t* dirichlet,
+                   const uint8_t* P, const double* psi, int K, int* mesh_id);
+
+/*
+ * Sizes of a registered mesh: info[0] n_nodes, [1] n_free (non-Dirichlet),
+ * [2] n_R (nodes the inner substeps update: P and its element neighbours),
+ * [3] n_P, [4] n_tri, [5] K, [6] number of node-element incidences.
+ */
+int lflts_mesh_info(lflts_ctx* ctx, int mesh_id, int64_t info[8]);
+
+/*
+ * Internal node order of a mesh: new2old [n_nodes] receives, for each
+ * internal position k, the caller's node index.  The order is
+ * [P nodes | R \ P | other free nodes | Dirichlet nodes], each group in the
+ * caller's order.  Works on host-only contexts (device -1).
+ */
+int lflts_mesh_order(lflts_ctx* ctx, int mesh_id, int32_t* new2old);
+
+/*
+ * Constants of the stabilised scheme (Sec. 3.3) as the library uses them,
+ * computed on the host in FP64 (no device needed):
+ *   out[0] delta = 1 + nu/p^2, out[1] omega = 2 T_p'(delta)/T_p(delta),
+ *   out[2] c0 = dt^2/(omega delta) (first substep, u-form),
+ *   out[3] gamma (the factor of the leapfrog update away from P, dt^2/2 in
+ *   exact arithmetic), then for m = 1..p-1:
+ *   out[4+2(m-1)] beta_m = T_{m-1}/T_{m+1},
+ *   out[5+2(m-1)] c_m = 2 dt^2 beta_{m+1/2} / omega.
+ * out must hold 4 + 2(p-1) doubles.
+ */
+int lflts_lts_constants(int p, double nu, double dt, double* out);
+
+/*
+ * Register a nodal field (initial displacement u0 or velocity v0, Sec. 2.1)
+ * on a mesh: values [n_nodes] FP64 in the caller's node order; values on
+ * Dirichlet nodes are replaced by 0.
+ */
+int lflts_field_add(lflts_ctx* ctx, int mesh_id, const double* values, int* field_id);
+
+/*
+ * Register a linear QoI Q(u) = sum_k g[k] u[idx[k]] on a mesh (Sec. 2.1,
+ * V = R).  idx [nnz] int32 node indices, g [nnz] FP64 weights.
+ */
+int lflts_qoi_add(lflts_ctx* ctx, int mesh_id, const int32_t* idx,
+                  const double* g, int64_t nnz, int* qoi_id);
+
+/* One level solve: the problem statement of Alg. 2 for a batch of draws. */
+typedef struct {
+  int mesh_id;      /* mesh from lflts_mesh_add                                */
+  int qoi_id;       /* QoI from lflts_qoi_add on the same mesh                 */
+  int u0_field;     /* initial displacement, field id on the same mesh        */
+  int v0_field;     /* initial velocity field id, or -1 for v0 = 0            */
+  int precision;    /* 32: FP32 state, FP64 QoI; 64: FP64 throughout          */
+  int p;            /* LTS ratio, 1 <= p <= 64 (p = 1: leapfrog)             */
+  double nu;        /* stabilisation parameter, 0 <= nu <= 1                  */
+  double dt;        /* coarse time step                                       */
+  int64_t n_steps;  /* N >= 1 steps; the QoI is taken at t_N = N dt           */
+} lflts_solve_desc;
+
+/*
+ * Solve the semidiscrete wave equation for S draws with stabilised LF-LTS
+ * (Alg. 2; start z_1 = q_1(z_0) + dt M^{1/2} v0) and evaluate the QoI at t_N.
+ *   xi   [S][K] FP64 draws (host or device per `mem`)
+ *   Q    [S] FP64 output, Q[s] = QoI of sample s
+ *   uN   optional [n_nodes][S] FP64 output of u_h(t_N) in the caller's node
+ *        order (same memory kind as Q), or NULL
+ * Errors: LFLTS_ERR_ARG for bad ids/sizes, LFLTS_ERR_UNSTABLE (host mode
+ * only) if some Q[s] is not finite; the message names the first such s.
+ */
+int lflts_solve(lflts_ctx* ctx, const lflts_solve_desc* desc, const double* xi,
+                int64_t S, double* Q, double* uN, int mem, void* stream);
+
+/*
+ * MLMC level sums (Sec. 2.2): with dQ = Qf - Qc (or Qf when Qc is NULL, the
+ * coarsest level), sums = {sum dQ, sum dQ^2, sum Qf, sum Qf^2} over the S
+ * samples, FP64 with compensated (Neumaier) summation in a fixed order.
+ * Qf, Qc [S] FP64; sums [4] FP64; all of the kind given by `mem`.
+ */
+int lflts_level_sums(lflts_ctx* ctx, const double* Qf, const double* Qc,
+                     int64_t S, double* sums, int mem, void* stream);
+
+/*
+ * One MLMC level pair (Alg. 1 step 2a): Q_l and Q_{l-1} of the same draws
+ * (the coarse solve is skipped when has_coarse == 0, level 0), the
+ * differences dQ and the level sums.  Solves that share mesh, QoI, fields,
+ * precision, p, nu, dt and n_steps across the jobs of one call are merged
+ * into a single batched solve.  Independent solves run concurrently on
+ * streams of the context, joined back into `stream`.
+ *   xi [S][K]; dQ, Qf [S] (Qf may be NULL); sums [4] (may be NULL).
+ */
+typedef struct {
+  lflts_solve_desc fine;
+  lflts_solve_desc coarse;
+  int has_coarse;
+  const double* xi;
+  int64_t S;
+  double* dQ;
+  double* Qf;
+  double* sums;
+} lflts_pair_job;
+
+int lflts_run_pairs(lflts_ctx* ctx, const lflts_pair_job* jobs, int n_jobs,
+                    int mem, void* stream);
+
+/*
+ * Profiling.  When enabled, every kernel launch is bracketed by CUDA events
+ * on its stream; lflts_profile_read synchronises the context's device and
+ * returns, per kernel class, the launch count, the summed device time in ms
+ * and the summed algorithmic bytes (the state traffic the method must move:
+ * per node and sample, FP32 state counts 4 bytes per value read or written;
+ * see the kernel class comments in the implementation).  Reset clears the
+ * counters.  lflts_launch_count returns all kernel launches of the context
+ * since creation, whether profiling is on or not.
+ */
+int lflts_profile_enable(lflts_ctx* ctx, int on);
+int lflts_profile_reset(lflts_ctx* ctx);
+int lflts_profile_read(lflts_ctx* ctx, int kernel_class, int64_t* launches,
+                       double* ms, double* alg_bytes);
+int lflts_launch_count(lflts_ctx* ctx, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LFLTS_H */

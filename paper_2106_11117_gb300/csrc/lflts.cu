@@ -1,0 +1,814 @@
+// C ABI of the LF-LTS / MLMC library (declared in include/lflts.h).
+//
+// Host orchestration of the kernels in kernels.cuh: mesh upload, per-solve
+// workspaces, the time loop of Alg. 2 (one coarse launch and p-1 inner
+// launches per step), the QoI reduction and the MLMC level sums, merged
+// batched solves for level pairs, profiling counters.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lflts.h"
+#include "kernels.cuh"
+#include "mesh_prep.h"
+
+using namespace lflts;
+
+namespace {
+
+// Largest batch: 65535 CTA rows of 32 samples (grid y limit).
+constexpr int64_t kMaxS = int64_t(65535) * 32;
+
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+struct MeshGPU {
+  HostMesh h;
+  int* inc_ptr = nullptr;
+  int4* inc = nullptr;
+  float2* w32 = nullptr;
+  double2* w64 = nullptr;
+  float* minv32 = nullptr;
+  double* minv64 = nullptr;
+  float* psi32 = nullptr;
+  double* psi64 = nullptr;
+  int* new2old = nullptr;
+};
+
+struct Field {
+  int mesh;
+  float* v32 = nullptr;
+  double* v64 = nullptr;
+};
+
+struct Qoi {
+  int mesh;
+  int nnz;
+  int* idx = nullptr;  // new node ids
+  double* g = nullptr;
+};
+
+struct Workspace {
+  Buf ua, ub, d, g, r0, r1, r2, xipad, xraw, qps, qpc, Q, uN;
+};
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+}  // namespace
+
+struct lflts_ctx {
+  int device = -1;  // -1: host-only context (mesh preparation, no solves)
+  int sms = 152;
+  std::string err;
+  std::vector<std::unique_ptr<MeshGPU>> meshes;
+  std::vector<Field> fields;
+  std::vector<Qoi> qois;
+  std::vector<std::unique_ptr<Workspace>> ws;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> sync_events;
+  int* d_bad = nullptr;
+  double* d_scratch = nullptr;  // small FP64 staging (sums)
+  bool profiling = false;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t prof_launches[LFLTS_KERNEL_CLASSES] = {0};
+  double prof_ms[LFLTS_KERNEL_CLASSES] = {0};
+  double prof_bytes[LFLTS_KERNEL_CLASSES] = {0};
+  int64_t launches = 0;
+  std::vector<void*> owned;  // device allocations of meshes, fields, QoIs
+};
+
+namespace {
+
+int fail(lflts_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define LF_CUDA(ctx, call)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? LFLTS_ERR_OOM : LFLTS_ERR_CUDA, \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+#define LF_TRY(expr)      \
+  do {                    \
+    int rc_ = (expr);     \
+    if (rc_ != 0) return rc_; \
+  } while (0)
+
+int ensure(lflts_ctx* c, Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.n >= bytes) return 0;
+  if (b.p) {
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+  }
+  LF_CUDA(c, cudaMalloc(&b.p, bytes));
+  b.n = bytes;
+  return 0;
+}
+
+template <typename T>
+int upload(lflts_ctx* c, T** dst, const T* src, size_t count) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  LF_CUDA(c, cudaMalloc((void**)dst, bytes));
+  c->owned.push_back(*dst);
+  if (count) LF_CUDA(c, cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+int set_device(lflts_ctx* c) {
+  if (c->device < 0) return fail(c, LFLTS_ERR_ARG, "host-only context: no device for this call");
+  LF_CUDA(c, cudaSetDevice(c->device));
+  return 0;
+}
+
+cudaEvent_t get_event(lflts_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct Prof {
+  lflts_ctx* c;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  Prof(lflts_ctx* c_, cudaStream_t st_) : c(c_), st(st_) {
+    if (c->profiling) {
+      a = get_event(c);
+      cudaEventRecord(a, st);
+    }
+  }
+  void end(int cls, double bytes) {
+    c->launches++;
+    if (c->profiling) {
+      cudaEvent_t b = get_event(c);
+      cudaEventRecord(b, st);
+      c->pending.push_back({cls, a, b, bytes});
+    }
+  }
+};
+
+// Chebyshev constants of the stabilised scheme (Sec. 3.3) and the derived
+// increment-form coefficients.  out: delta, omega, c0, gamma, then for
+// m = 1..p-1: beta_m, c_m.
+void lts_constants(int p, double nu, double dt, std::vector<double>& beta, std::vector<double>& cm,
+                   double& delta, double& omega, double& c0, double& gamma) {
+  delta = 1.0 + nu / (double(p) * p);
+  std::vector<double> T(p + 2), U(p + 2);
+  T[0] = 1.0;
+  T[1] = delta;
+  for (int k = 1; k <= p; ++k) T[k + 1] = 2.0 * delta * T[k] - T[k - 1];
+  U[0] = 1.0;
+  U[1] = 2.0 * delta;
+  for (int k = 1; k <= p; ++k) U[k + 1] = 2.0 * delta * U[k] - U[k - 1];
+  const double Tp_prime = p * U[p - 1];
+  omega = 2.0 * Tp_prime / T[p];
+  c0 = dt * dt / (omega * delta);
+  beta.assign(p, 0.0);
+  cm.assign(p, 0.0);
+  for (int m = 1; m < p; ++m) {
+    beta[m] = T[m - 1] / T[m + 1];
+    cm[m] = 2.0 * dt * dt * (T[m] / T[m + 1]) / omega;
+  }
+  // gamma: the same recursion for a node whose AP-term vanishes, with g = 1
+  double r_prev = 0.0, r = -c0;
+  for (int m = 1; m < p; ++m) {
+    const double rn = (1.0 + beta[m]) * r - beta[m] * r_prev - cm[m];
+    r_prev = r;
+    r = rn;
+  }
+  gamma = -r;
+}
+
+struct Geo {
+  dim3 grid;
+  int SB;
+};
+
+Geo geometry(const lflts_ctx* c, int64_t n, int64_t S) {
+  int SB = 1;
+  while (SB < 32 && SB * 2 <= S) SB *= 2;
+  const int NB = 256 / SB;
+  const int64_t gy = (S + SB - 1) / SB;
+  const int64_t target = int64_t(c->sms) * 16;
+  int64_t gx = std::max<int64_t>(1, std::min<int64_t>((n + NB - 1) / NB, std::max<int64_t>(1, target / gy)));
+  Geo g;
+  g.grid = dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy), 1);
+  g.SB = SB;
+  return g;
+}
+
+int blocks_for(int64_t total, int threads, int cap) {
+  int64_t b = (total + threads - 1) / threads;
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(b, cap)));
+}
+
+template <typename Real>
+struct Sel;
+template <>
+struct Sel<float> {
+  static MeshDev<float> mesh(const MeshGPU& m, int n_R) {
+    return MeshDev<float>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.inc_ptr, m.inc, m.w32, m.minv32, m.psi32};
+  }
+  static const float* field(const Field& f) { return f.v32; }
+};
+template <>
+struct Sel<double> {
+  static MeshDev<double> mesh(const MeshGPU& m, int n_R) {
+    return MeshDev<double>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.inc_ptr, m.inc, m.w64, m.minv64, m.psi64};
+  }
+  static const double* field(const Field& f) { return f.v64; }
+};
+
+template <typename Real, int KP>
+int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, const Qoi& q,
+                 const Field& u0, const Field* v0, const double* d_xi, int64_t S, double* d_Q,
+                 double* d_uN, Workspace& ws, cudaStream_t st) {
+  const HostMesh& h = mg.h;
+  const size_t rb = sizeof(Real);
+  const int64_t n_nodes = h.n_nodes;
+  const int p = ds.p;
+  const int n_R = (p > 1) ? static_cast<int>(h.n_R) : 0;
+  const size_t state_bytes = size_t(n_nodes) * S * rb;
+  const size_t r_bytes = size_t(std::max(n_R, 1)) * S * rb;
+  LF_TRY(ensure(c, ws.ua, state_bytes));
+  LF_TRY(ensure(c, ws.ub, state_bytes));
+  LF_TRY(ensure(c, ws.d, state_bytes));
+  LF_TRY(ensure(c, ws.g, r_bytes));
+  LF_TRY(ensure(c, ws.r0, r_bytes));
+  LF_TRY(ensure(c, ws.r1, r_bytes));
+  LF_TRY(ensure(c, ws.r2, r_bytes));
+  LF_TRY(ensure(c, ws.xipad, size_t(S) * KP * rb));
+  Real* ua = static_cast<Real*>(ws.ua.p);
+  Real* ub = static_cast<Real*>(ws.ub.p);
+  Real* d = static_cast<Real*>(ws.d.p);
+  Real* g = static_cast<Real*>(ws.g.p);
+  Real* rbuf[3] = {static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p)};
+  Real* xi = static_cast<Real*>(ws.xipad.p);
+
+  {
+    Prof pr(c, st);
+    k_xi_pad<Real, KP><<<blocks_for(S * KP, 256, 4096), 256, 0, st>>>((int)S, h.K, d_xi, xi);
+    LF_CUDA(c, cudaGetLastError());
+    k_init_state<Real><<<blocks_for(n_nodes * S, 256, c->sms * 32), 256, 0, st>>>(
+        n_nodes, (int)S, Sel<Real>::field(u0), v0 ? Sel<Real>::field(*v0) : nullptr, (Real)ds.dt, ua, ub, d);
+    LF_CUDA(c, cudaGetLastError());
+    pr.end(LFLTS_KERNEL_INIT, double(n_nodes) * S * rb * 3);
+    c->launches++;  // two kernels in this class
+  }
+
+  std::vector<double> beta, cm;
+  double delta, omega, c0, gamma;
+  lts_constants(p, ds.nu, ds.dt, beta, cm, delta, omega, c0, gamma);
+  const MeshDev<Real> md = Sel<Real>::mesh(mg, n_R);
+  const Geo gc = geometry(c, h.n_free, S);
+  const Geo gi = geometry(c, std::max(n_R, 1), S);
+  const double coarse_bytes = double(S) * rb * (4.0 * h.n_free - n_R);
+
+  Real* uc = ua;
+  Real* un = ub;
+  for (int64_t n = 0; n < ds.n_steps; ++n) {
+    const Real kappa = (n == 0) ? Real(1) : Real(2);
+    {
+      Prof pr(c, st);
+      k_coarse<Real, KP><<<gc.grid, 256, 0, st>>>(md, xi, (int)S, gc.SB, uc, un, d, g, rbuf[0],
+                                                   (Real)(double(kappa) * gamma), (Real)c0);
+      LF_CUDA(c, cudaGetLastError());
+      pr.end(LFLTS_KERNEL_COARSE, coarse_bytes);
+    }
+    if (n_R > 0) {
+      int cur = 0, prev = -1;
+      for (int m = 1; m < p; ++m) {
+        const int nxt = (cur + 1) % 3 == prev ? (cur + 2) % 3 : (cur + 1) % 3;
+        const bool first = (m == 1), last = (m == p - 1);
+        const Real* rp = prev >= 0 ? rbuf[prev] : nullptr;
+        const Real opb = (Real)(1.0 + beta[m]), bt = (Real)beta[m], cmm = (Real)cm[m];
+        Prof pr(c, st);
+        if (first && last)
+          k_inner<Real, KP, true, true><<<gi.grid, 256, 0, st>>>(md, xi, (int)S, gi.SB, rbuf[cur], rp, rbuf[nxt], g, uc, un, d, opb, bt, cmm, kappa);
+        else if (first)
+          k_inner<Real, KP, true, false><<<gi.grid, 256, 0, st>>>(md, xi, (int)S, gi.SB, rbuf[cur], rp, rbuf[nxt], g, uc, un, d, opb, bt, cmm, kappa);
+        else if (last)
+          k_inner<Real, KP, false, true><<<gi.grid, 256, 0, st>>>(md, xi, (int)S, gi.SB, rbuf[cur], rp, rbuf[nxt], g, uc, un, d, opb, bt, cmm, kappa);
+        else
+          k_inner<Real, KP, false, false><<<gi.grid, 256, 0, st>>>(md, xi, (int)S, gi.SB, rbuf[cur], rp, rbuf[nxt], g, uc, un, d, opb, bt, cmm, kappa);
+        LF_CUDA(c, cudaGetLastError());
+        const double per_node = last ? (first ? 6.0 : 7.0) : (first ? 3.0 : 4.0);
+        pr.end(LFLTS_KERNEL_INNER, per_node * n_R * double(S) * rb);
+        prev = cur;
+        cur = nxt;
+      }
+    }
+    std::swap(uc, un);
+  }
+
+  // QoI at t_N (Sec. 2.1), FP64 compensated accumulation.
+  {
+    const int chunk = 512;
+    const int n_chunks = std::max(1, (q.nnz + chunk - 1) / chunk);
+    LF_TRY(ensure(c, ws.qps, size_t(n_chunks) * S * sizeof(double)));
+    LF_TRY(ensure(c, ws.qpc, size_t(n_chunks) * S * sizeof(double)));
+    const int tb = static_cast<int>(std::min<int64_t>(S, 128));
+    Prof pr(c, st);
+    k_qoi_partial<Real><<<dim3(n_chunks, static_cast<unsigned>((S + tb - 1) / tb)), tb, 0, st>>>(
+        uc, (int)S, q.idx, q.g, q.nnz, chunk, static_cast<double*>(ws.qps.p), static_cast<double*>(ws.qpc.p));
+    LF_CUDA(c, cudaGetLastError());
+    k_qoi_final<<<blocks_for(S, 128, 1 << 20), 128, 0, st>>>(n_chunks, (int)S, static_cast<double*>(ws.qps.p),
+                                                            static_cast<double*>(ws.qpc.p), d_Q, c->d_bad);
+    LF_CUDA(c, cudaGetLastError());
+    pr.end(LFLTS_KERNEL_QOI, double(q.nnz) * S * rb);
+    c->launches++;
+  }
+  if (d_uN) {
+    k_gather_state<Real><<<blocks_for(n_nodes * S, 256, c->sms * 32), 256, 0, st>>>(n_nodes, (int)S, mg.new2old, uc, d_uN);
+    LF_CUDA(c, cudaGetLastError());
+    c->launches++;
+  }
+  return 0;
+}
+
+template <typename Real>
+int run_solve(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64_t S, double* d_Q,
+              double* d_uN, Workspace& ws, cudaStream_t st) {
+  const MeshGPU& mg = *c->meshes[ds.mesh_id];
+  const Qoi& q = c->qois[ds.qoi_id];
+  const Field& u0 = c->fields[ds.u0_field];
+  const Field* v0 = ds.v0_field >= 0 ? &c->fields[ds.v0_field] : nullptr;
+  switch (mg.h.KP) {
+    case 4: return run_solve_kp<Real, 4>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st);
+    case 8: return run_solve_kp<Real, 8>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st);
+    default: return run_solve_kp<Real, 16>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st);
+  }
+}
+
+int check_desc(lflts_ctx* c, const lflts_solve_desc* ds) {
+  if (!ds) return fail(c, LFLTS_ERR_ARG, "solve: null descriptor");
+  if (ds->mesh_id < 0 || ds->mesh_id >= (int)c->meshes.size()) return fail(c, LFLTS_ERR_ARG, "solve: bad mesh_id");
+  if (ds->qoi_id < 0 || ds->qoi_id >= (int)c->qois.size() || c->qois[ds->qoi_id].mesh != ds->mesh_id)
+    return fail(c, LFLTS_ERR_ARG, "solve: qoi_id does not belong to the mesh");
+  if (ds->u0_field < 0 || ds->u0_field >= (int)c->fields.size() || c->fields[ds->u0_field].mesh != ds->mesh_id)
+    return fail(c, LFLTS_ERR_ARG, "solve: u0_field does not belong to the mesh");
+  if (ds->v0_field >= 0 && (ds->v0_field >= (int)c->fields.size() || c->fields[ds->v0_field].mesh != ds->mesh_id))
+    return fail(c, LFLTS_ERR_ARG, "solve: v0_field does not belong to the mesh");
+  if (ds->precision != 32 && ds->precision != 64) return fail(c, LFLTS_ERR_ARG, "solve: precision must be 32 or 64");
+  if (ds->p < 1 || ds->p > 64) return fail(c, LFLTS_ERR_ARG, "solve: p must be in [1, 64]");
+  if (!(ds->nu >= 0.0 && ds->nu <= 1.0)) return fail(c, LFLTS_ERR_ARG, "solve: nu must be in [0, 1]");
+  if (!(ds->dt > 0.0) || !std::isfinite(ds->dt)) return fail(c, LFLTS_ERR_ARG, "solve: dt must be positive");
+  if (ds->n_steps < 1) return fail(c, LFLTS_ERR_ARG, "solve: n_steps must be >= 1");
+  return 0;
+}
+
+int solve_device(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64_t S, double* d_Q,
+                 double* d_uN, Workspace& ws, cudaStream_t st) {
+  if (ds.precision == 32) return run_solve<float>(c, ds, d_xi, S, d_Q, d_uN, ws, st);
+  return run_solve<double>(c, ds, d_xi, S, d_Q, d_uN, ws, st);
+}
+
+Workspace& workspace(lflts_ctx* c, size_t slot) {
+  while (c->ws.size() <= slot) c->ws.emplace_back(new Workspace());
+  return *c->ws[slot];
+}
+
+int reset_bad(lflts_ctx* c, cudaStream_t st) {
+  LF_CUDA(c, cudaMemsetAsync(c->d_bad, 0x7f, sizeof(int), st));
+  return 0;
+}
+
+int check_bad(lflts_ctx* c, cudaStream_t st) {
+  int bad = INT_MAX;
+  LF_CUDA(c, cudaMemcpyAsync(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LF_CUDA(c, cudaStreamSynchronize(st));
+  if (bad != 0x7f7f7f7f)
+    return fail(c, LFLTS_ERR_UNSTABLE, "non-finite QoI (unstable solve), first sample " + std::to_string(bad));
+  return 0;
+}
+
+}  // namespace
+
+// ============================================================================
+// ABI
+// ============================================================================
+extern "C" {
+
+int lflts_version(void) { return 100; }
+
+int lflts_create(lflts_ctx** out, int device) {
+  if (!out) return LFLTS_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<lflts_ctx> c(new lflts_ctx());
+  c->device = device;
+  if (device >= 0) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device >= n) return LFLTS_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return LFLTS_ERR_CUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return LFLTS_ERR_CUDA;
+    c->sms = prop.multiProcessorCount;
+    if (cudaMalloc(&c->d_bad, sizeof(int)) != cudaSuccess) return LFLTS_ERR_OOM;
+    if (cudaMalloc(&c->d_scratch, 64 * sizeof(double)) != cudaSuccess) return LFLTS_ERR_OOM;
+  }
+  *out = c.release();
+  return LFLTS_OK;
+}
+
+int lflts_destroy(lflts_ctx* c) {
+  if (!c) return LFLTS_OK;
+  if (c->device >= 0) {
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto& w : c->ws)
+      for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->xipad, &w->xraw, &w->qps,
+                     &w->qpc, &w->Q, &w->uN})
+        if (b->p) cudaFree(b->p);
+    for (void* p : c->owned) cudaFree(p);
+    for (auto s : c->streams) cudaStreamDestroy(s);
+    for (auto e : c->sync_events) cudaEventDestroy(e);
+    for (auto& r : c->pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : c->pool) cudaEventDestroy(e);
+    if (c->d_bad) cudaFree(c->d_bad);
+    if (c->d_scratch) cudaFree(c->d_scratch);
+  }
+  delete c;
+  return LFLTS_OK;
+}
+
+const char* lflts_last_error(const lflts_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int lflts_mesh_add(lflts_ctx* c, const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
+                   const uint8_t* dirichlet, const uint8_t* P, const double* psi, int K, int* mesh_id) {
+  if (!c || !mesh_id) return LFLTS_ERR_ARG;
+  c->err.clear();
+  std::unique_ptr<MeshGPU> mg(new MeshGPU());
+  int rc = prep_mesh(xy, n_nodes, tri, n_tri, dirichlet, P, psi, K, mg->h, c->err);
+  if (rc) return rc;
+  if (c->device >= 0) {
+    LF_TRY(set_device(c));
+    const HostMesh& h = mg->h;
+    const size_t ni = h.inc_e.size();
+    std::vector<int4> inc(ni);
+    std::vector<float2> w32(ni);
+    std::vector<double2> w64(ni);
+    for (size_t t = 0; t < ni; ++t) {
+      inc[t] = make_int4(h.inc_e[t], h.inc_j1[t], h.inc_j2[t], 0);
+      w32[t] = make_float2((float)h.inc_w1[t], (float)h.inc_w2[t]);
+      w64[t] = make_double2(h.inc_w1[t], h.inc_w2[t]);
+    }
+    std::vector<float> minv32(h.minv.begin(), h.minv.end());
+    std::vector<float> psi32(h.psi2.begin(), h.psi2.end());
+    LF_TRY(upload(c, &mg->inc_ptr, h.inc_ptr.data(), h.inc_ptr.size()));
+    LF_TRY(upload(c, &mg->inc, inc.data(), ni));
+    LF_TRY(upload(c, &mg->w32, w32.data(), ni));
+    LF_TRY(upload(c, &mg->w64, w64.data(), ni));
+    LF_TRY(upload(c, &mg->minv32, minv32.data(), minv32.size()));
+    LF_TRY(upload(c, &mg->minv64, h.minv.data(), h.minv.size()));
+    LF_TRY(upload(c, &mg->psi32, psi32.data(), psi32.size()));
+    LF_TRY(upload(c, &mg->psi64, h.psi2.data(), h.psi2.size()));
+    LF_TRY(upload(c, &mg->new2old, h.new2old.data(), h.new2old.size()));
+  }
+  *mesh_id = static_cast<int>(c->meshes.size());
+  c->meshes.push_back(std::move(mg));
+  return LFLTS_OK;
+}
+
+int lflts_mesh_info(lflts_ctx* c, int mesh_id, int64_t info[8]) {
+  if (!c || !info) return LFLTS_ERR_ARG;
+  if (mesh_id < 0 || mesh_id >= (int)c->meshes.size()) return fail(c, LFLTS_ERR_ARG, "mesh_info: bad mesh_id");
+  const HostMesh& h = c->meshes[mesh_id]->h;
+  info[0] = h.n_nodes;
+  info[1] = h.n_free;
+  info[2] = h.n_R;
+  info[3] = h.n_P;
+  info[4] = h.n_tri;
+  info[5] = h.K;
+  info[6] = static_cast<int64_t>(h.inc_e.size());
+  info[7] = h.KP;
+  return LFLTS_OK;
+}
+
+int lflts_mesh_order(lflts_ctx* c, int mesh_id, int32_t* new2old) {
+  if (!c || !new2old) return LFLTS_ERR_ARG;
+  if (mesh_id < 0 || mesh_id >= (int)c->meshes.size()) return fail(c, LFLTS_ERR_ARG, "mesh_order: bad mesh_id");
+  const HostMesh& h = c->meshes[mesh_id]->h;
+  std::memcpy(new2old, h.new2old.data(), h.new2old.size() * sizeof(int32_t));
+  return LFLTS_OK;
+}
+
+int lflts_lts_constants(int p, double nu, double dt, double* out) {
+  if (!out || p < 1 || p > 64 || !(nu >= 0.0 && nu <= 1.0) || !(dt > 0.0)) return LFLTS_ERR_ARG;
+  std::vector<double> beta, cm;
+  double delta, omega, c0, gamma;
+  lts_constants(p, nu, dt, beta, cm, delta, omega, c0, gamma);
+  out[0] = delta;
+  out[1] = omega;
+  out[2] = c0;
+  out[3] = gamma;
+  for (int m = 1; m < p; ++m) {
+    out[4 + 2 * (m - 1)] = beta[m];
+    out[5 + 2 * (m - 1)] = cm[m];
+  }
+  return LFLTS_OK;
+}
+
+int lflts_field_add(lflts_ctx* c, int mesh_id, const double* values, int* field_id) {
+  if (!c || !values || !field_id) return LFLTS_ERR_ARG;
+  if (mesh_id < 0 || mesh_id >= (int)c->meshes.size()) return fail(c, LFLTS_ERR_ARG, "field_add: bad mesh_id");
+  LF_TRY(set_device(c));
+  const HostMesh& h = c->meshes[mesh_id]->h;
+  std::vector<double> v64(h.n_nodes, 0.0);
+  for (int64_t k = 0; k < h.n_free; ++k) {
+    const double v = values[h.new2old[k]];
+    if (!std::isfinite(v)) return fail(c, LFLTS_ERR_ARG, "field_add: non-finite value");
+    v64[k] = v;
+  }
+  std::vector<float> v32(v64.begin(), v64.end());
+  Field f;
+  f.mesh = mesh_id;
+  LF_TRY(upload(c, &f.v64, v64.data(), v64.size()));
+  LF_TRY(upload(c, &f.v32, v32.data(), v32.size()));
+  *field_id = static_cast<int>(c->fields.size());
+  c->fields.push_back(f);
+  return LFLTS_OK;
+}
+
+int lflts_qoi_add(lflts_ctx* c, int mesh_id, const int32_t* idx, const double* g, int64_t nnz, int* qoi_id) {
+  if (!c || !qoi_id || (nnz > 0 && (!idx || !g)) || nnz < 0 || nnz >= INT_MAX) return LFLTS_ERR_ARG;
+  if (mesh_id < 0 || mesh_id >= (int)c->meshes.size()) return fail(c, LFLTS_ERR_ARG, "qoi_add: bad mesh_id");
+  LF_TRY(set_device(c));
+  const HostMesh& h = c->meshes[mesh_id]->h;
+  std::vector<int32_t> nid(nnz);
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (idx[k] < 0 || idx[k] >= h.n_nodes) return fail(c, LFLTS_ERR_ARG, "qoi_add: index out of range");
+    if (!std::isfinite(g[k])) return fail(c, LFLTS_ERR_ARG, "qoi_add: non-finite weight");
+    nid[k] = h.old2new[idx[k]];
+  }
+  Qoi q;
+  q.mesh = mesh_id;
+  q.nnz = static_cast<int>(nnz);
+  LF_TRY(upload(c, &q.idx, nid.data(), nid.size()));
+  LF_TRY(upload(c, &q.g, g, static_cast<size_t>(nnz)));
+  *qoi_id = static_cast<int>(c->qois.size());
+  c->qois.push_back(q);
+  return LFLTS_OK;
+}
+
+int lflts_solve(lflts_ctx* c, const lflts_solve_desc* ds, const double* xi, int64_t S, double* Q, double* uN,
+                int mem, void* stream) {
+  if (!c) return LFLTS_ERR_ARG;
+  c->err.clear();
+  LF_TRY(set_device(c));
+  LF_TRY(check_desc(c, ds));
+  if (S < 1 || S > kMaxS) return fail(c, LFLTS_ERR_ARG, "solve: S must be in [1, 2097120]");
+  if (!xi || !Q) return fail(c, LFLTS_ERR_ARG, "solve: null xi or Q");
+  if (mem != LFLTS_MEM_HOST && mem != LFLTS_MEM_DEVICE) return fail(c, LFLTS_ERR_ARG, "solve: bad mem kind");
+  const HostMesh& h = c->meshes[ds->mesh_id]->h;
+  if (double(h.n_nodes) * double(S) >= 9.0e18) return fail(c, LFLTS_ERR_ARG, "solve: state too large");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Workspace& ws = workspace(c, 0);
+  LF_TRY(reset_bad(c, st));
+  if (mem == LFLTS_MEM_DEVICE) return solve_device(c, *ds, xi, S, Q, uN, ws, st);
+  // host buffers: stage xi, run, copy results back, synchronise
+  LF_TRY(ensure(c, ws.xraw, size_t(S) * h.K * sizeof(double)));
+  LF_TRY(ensure(c, ws.Q, size_t(S) * sizeof(double)));
+  if (uN) LF_TRY(ensure(c, ws.uN, size_t(h.n_nodes) * S * sizeof(double)));
+  LF_CUDA(c, cudaMemcpyAsync(ws.xraw.p, xi, size_t(S) * h.K * sizeof(double), cudaMemcpyHostToDevice, st));
+  LF_TRY(solve_device(c, *ds, static_cast<double*>(ws.xraw.p), S, static_cast<double*>(ws.Q.p),
+                      uN ? static_cast<double*>(ws.uN.p) : nullptr, ws, st));
+  LF_CUDA(c, cudaMemcpyAsync(Q, ws.Q.p, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (uN) LF_CUDA(c, cudaMemcpyAsync(uN, ws.uN.p, size_t(h.n_nodes) * S * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return check_bad(c, st);
+}
+
+int lflts_level_sums(lflts_ctx* c, const double* Qf, const double* Qc, int64_t S, double* sums, int mem,
+                     void* stream) {
+  if (!c) return LFLTS_ERR_ARG;
+  c->err.clear();
+  LF_TRY(set_device(c));
+  if (!Qf || !sums || S < 1) return fail(c, LFLTS_ERR_ARG, "level_sums: null array or S < 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (mem == LFLTS_MEM_DEVICE) {
+    Prof pr(c, st);
+    k_level_sums<<<1, 256, 0, st>>>(S, Qf, Qc, sums);
+    LF_CUDA(c, cudaGetLastError());
+    pr.end(LFLTS_KERNEL_SUMS, double(S) * (Qc ? 16.0 : 8.0));
+    return LFLTS_OK;
+  }
+  Workspace& ws = workspace(c, 0);
+  LF_TRY(ensure(c, ws.Q, size_t(S) * 2 * sizeof(double)));
+  double* dQf = static_cast<double*>(ws.Q.p);
+  double* dQc = Qc ? dQf + S : nullptr;
+  LF_CUDA(c, cudaMemcpyAsync(dQf, Qf, size_t(S) * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (Qc) LF_CUDA(c, cudaMemcpyAsync(dQc, Qc, size_t(S) * sizeof(double), cudaMemcpyHostToDevice, st));
+  {
+    Prof pr(c, st);
+    k_level_sums<<<1, 256, 0, st>>>(S, dQf, dQc, c->d_scratch);
+    LF_CUDA(c, cudaGetLastError());
+    pr.end(LFLTS_KERNEL_SUMS, double(S) * (Qc ? 16.0 : 8.0));
+  }
+  LF_CUDA(c, cudaMemcpyAsync(sums, c->d_scratch, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  LF_CUDA(c, cudaStreamSynchronize(st));
+  return LFLTS_OK;
+}
+
+int lflts_run_pairs(lflts_ctx* c, const lflts_pair_job* jobs, int n_jobs, int mem, void* stream) {
+  if (!c) return LFLTS_ERR_ARG;
+  c->err.clear();
+  LF_TRY(set_device(c));
+  if (!jobs || n_jobs < 1) return fail(c, LFLTS_ERR_ARG, "run_pairs: no jobs");
+  if (mem != LFLTS_MEM_HOST && mem != LFLTS_MEM_DEVICE) return fail(c, LFLTS_ERR_ARG, "run_pairs: bad mem kind");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  // ---- group identical solves ----------------------------------------------
+  struct Member { int job; bool fine; int64_t off; };
+  struct Group { lflts_solve_desc desc; int64_t S = 0; std::vector<Member> members; };
+  std::vector<Group> groups;
+  auto key_eq = [](const lflts_solve_desc& a, const lflts_solve_desc& b) {
+    return a.mesh_id == b.mesh_id && a.qoi_id == b.qoi_id && a.u0_field == b.u0_field &&
+           a.v0_field == b.v0_field && a.precision == b.precision && a.p == b.p && a.nu == b.nu &&
+           a.dt == b.dt && a.n_steps == b.n_steps;
+  };
+  auto add_member = [&](const lflts_solve_desc& ds, int j, bool fine, int64_t S) {
+    for (auto& gr : groups)
+      if (key_eq(gr.desc, ds)) {
+        gr.members.push_back({j, fine, gr.S});
+        gr.S += S;
+        return;
+      }
+    Group gr;
+    gr.desc = ds;
+    gr.members.push_back({j, fine, 0});
+    gr.S = S;
+    groups.push_back(gr);
+  };
+  for (int j = 0; j < n_jobs; ++j) {
+    const lflts_pair_job& jb = jobs[j];
+    if (!jb.xi || !jb.dQ || jb.S < 1) return fail(c, LFLTS_ERR_ARG, "run_pairs: job " + std::to_string(j) + " has null xi/dQ or S < 1");
+    LF_TRY(check_desc(c, &jb.fine));
+    if (jb.has_coarse) {
+      LF_TRY(check_desc(c, &jb.coarse));
+      if (c->meshes[jb.coarse.mesh_id]->h.K != c->meshes[jb.fine.mesh_id]->h.K)
+        return fail(c, LFLTS_ERR_ARG, "run_pairs: fine and coarse meshes have different K");
+    }
+    add_member(jb.fine, j, true, jb.S);
+    if (jb.has_coarse) add_member(jb.coarse, j, false, jb.S);
+  }
+  for (auto& gr : groups)
+    if (gr.S > kMaxS) return fail(c, LFLTS_ERR_ARG, "run_pairs: merged batch larger than 2097120 samples");
+
+  // ---- streams and events ----------------------------------------------------
+  const size_t ng = groups.size();
+  while (c->streams.size() < ng) {
+    cudaStream_t s;
+    LF_CUDA(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    c->streams.push_back(s);
+  }
+  while (c->sync_events.size() < ng + 1) {
+    cudaEvent_t e;
+    LF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->sync_events.push_back(e);
+  }
+  LF_TRY(reset_bad(c, st));
+  LF_CUDA(c, cudaEventRecord(c->sync_events[ng], st));
+
+  // ---- per group: gather xi, solve ------------------------------------------
+  for (size_t gi = 0; gi < ng; ++gi) {
+    Group& gr = groups[gi];
+    Workspace& ws = workspace(c, 1 + gi);
+    const int K = c->meshes[gr.desc.mesh_id]->h.K;
+    cudaStream_t gs = c->streams[gi];
+    LF_CUDA(c, cudaStreamWaitEvent(gs, c->sync_events[ng], 0));
+    LF_TRY(ensure(c, ws.xraw, size_t(gr.S) * K * sizeof(double)));
+    LF_TRY(ensure(c, ws.Q, size_t(gr.S) * sizeof(double)));
+    for (const Member& mb : gr.members) {
+      const lflts_pair_job& jb = jobs[mb.job];
+      LF_CUDA(c, cudaMemcpyAsync(static_cast<double*>(ws.xraw.p) + mb.off * K, jb.xi, size_t(jb.S) * K * sizeof(double),
+                                 mem == LFLTS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, gs));
+    }
+    LF_TRY(solve_device(c, gr.desc, static_cast<double*>(ws.xraw.p), gr.S, static_cast<double*>(ws.Q.p), nullptr, ws, gs));
+    LF_CUDA(c, cudaEventRecord(c->sync_events[gi], gs));
+  }
+  for (size_t gi = 0; gi < ng; ++gi) LF_CUDA(c, cudaStreamWaitEvent(st, c->sync_events[gi], 0));
+
+  // ---- per job: dQ, Qf and level sums on the caller's stream ----------------
+  Workspace& ws0 = workspace(c, 0);
+  int64_t total = 0;
+  for (int j = 0; j < n_jobs; ++j) total += jobs[j].S;
+  if (mem == LFLTS_MEM_HOST) LF_TRY(ensure(c, ws0.Q, size_t(total) * 2 * sizeof(double) + 4 * sizeof(double) * n_jobs));
+  int64_t hoff = 0;
+  for (int j = 0; j < n_jobs; ++j) {
+    const lflts_pair_job& jb = jobs[j];
+    const double* qf = nullptr;
+    const double* qc = nullptr;
+    for (size_t gi = 0; gi < ng; ++gi)
+      for (const Member& mb : groups[gi].members)
+        if (mb.job == j) {
+          const double* base = static_cast<double*>(workspace(c, 1 + gi).Q.p) + mb.off;
+          if (mb.fine) qf = base;
+          else qc = base;
+        }
+    double* dq_dst = jb.dQ;
+    double* qf_dst = jb.Qf;
+    double* sums_dst = jb.sums;
+    if (mem == LFLTS_MEM_HOST) {
+      double* base = static_cast<double*>(ws0.Q.p);
+      dq_dst = base + hoff;
+      qf_dst = base + total + hoff;
+      sums_dst = base + 2 * total + 4 * j;
+    }
+    {
+      Prof pr(c, st);
+      k_pair_diff<<<blocks_for(jb.S, 128, 1 << 20), 128, 0, st>>>((int)jb.S, qf, qc, dq_dst, qf_dst);
+      LF_CUDA(c, cudaGetLastError());
+      k_level_sums<<<1, 256, 0, st>>>(jb.S, qf, qc, sums_dst);
+      LF_CUDA(c, cudaGetLastError());
+      pr.end(LFLTS_KERNEL_SUMS, double(jb.S) * 8.0 * (qc ? 5.0 : 3.0));
+      c->launches++;
+    }
+    if (mem == LFLTS_MEM_HOST) {
+      LF_CUDA(c, cudaMemcpyAsync(jb.dQ, dq_dst, size_t(jb.S) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      if (jb.Qf) LF_CUDA(c, cudaMemcpyAsync(jb.Qf, qf_dst, size_t(jb.S) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      if (jb.sums) LF_CUDA(c, cudaMemcpyAsync(jb.sums, sums_dst, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    hoff += jb.S;
+  }
+  if (mem == LFLTS_MEM_HOST) return check_bad(c, st);
+  return LFLTS_OK;
+}
+
+int lflts_profile_enable(lflts_ctx* c, int on) {
+  if (!c) return LFLTS_ERR_ARG;
+  c->profiling = on != 0;
+  return LFLTS_OK;
+}
+
+static int drain(lflts_ctx* c) {
+  if (c->pending.empty()) return 0;
+  LF_TRY(set_device(c));
+  LF_CUDA(c, cudaDeviceSynchronize());
+  for (auto& r : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.cls] += ms;
+      c->prof_bytes[r.cls] += r.bytes;
+      c->prof_launches[r.cls] += 1;
+    }
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->pending.clear();
+  return 0;
+}
+
+int lflts_profile_reset(lflts_ctx* c) {
+  if (!c) return LFLTS_ERR_ARG;
+  LF_TRY(drain(c));
+  for (int k = 0; k < LFLTS_KERNEL_CLASSES; ++k) {
+    c->prof_launches[k] = 0;
+    c->prof_ms[k] = 0;
+    c->prof_bytes[k] = 0;
+  }
+  return LFLTS_OK;
+}
+
+int lflts_profile_read(lflts_ctx* c, int cls, int64_t* launches, double* ms, double* bytes) {
+  if (!c || cls < 0 || cls >= LFLTS_KERNEL_CLASSES) return LFLTS_ERR_ARG;
+  LF_TRY(drain(c));
+  if (launches) *launches = c->prof_launches[cls];
+  if (ms) *ms = c->prof_ms[cls];
+  if (bytes) *bytes = c->prof_bytes[cls];
+  return LFLTS_OK;
+}
+
+int lflts_launch_count(lflts_ctx* c, int64_t* launches) {
+  if (!c || !launches) return LFLTS_ERR_ARG;
+  *launches = c->launches;
+  return LFLTS_OK;
+}
+
+}  // extern "C"

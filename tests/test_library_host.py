@@ -1,0 +1,110 @@
+"""Host-side checks of liblflts (no GPU): the library builds, loads and
+exports every symbol include/lflts.h declares; its host-only functions (LTS
+constants, mesh preparation on a host-only context) agree with the oracle
+and with the mask rule."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_11117_gb300 import build, lflts
+    build.build()
+    return lflts
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lflts.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lflts_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    lib.load()
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (lflts_[a-z_]+)", out))
+    declared = _declared()
+    assert declared, "no declarations parsed"
+    missing = [d for d in declared if d not in exported]
+    assert not missing, missing
+    assert set(lib.EXPORTED) == set(declared)
+
+
+@pytest.mark.parametrize("p,nu", [(1, 0.0), (2, 0.01), (4, 0.01), (8, 0.5), (16, 0.01)])
+def test_library_constants_match_oracle(lib, p, nu):
+    from oracle.lts import lts_constants
+    dt = 3.7e-3
+    L = lib.lflts_lts_constants(p, nu, dt)
+    O = lts_constants(p, nu)
+    assert L["delta"] == pytest.approx(O["delta"], rel=1e-15)
+    assert L["omega"] == pytest.approx(O["omega"], rel=1e-14)
+    # u-form coefficients of Alg. 2: c0 = 1/2 (dt/p)^2 2p^2/(omega delta), c_m = (dt/p)^2 2p^2/omega beta_{m+1/2}
+    assert L["c0"] == pytest.approx(0.5 * (dt / p) ** 2 * 2 * p * p / (O["omega"] * O["delta"]), rel=1e-14)
+    for m in range(1, p):
+        assert L["beta"][m] == pytest.approx(O["beta"][m], rel=1e-14)
+        assert L["c"][m] == pytest.approx((dt / p) ** 2 * 2 * p * p / O["omega"] * O["beta_half"][m], rel=1e-14)
+    # away from P the scheme is leapfrog: the factor is dt^2 / 2 (Sec. 3.3)
+    assert L["gamma"] == pytest.approx(0.5 * dt * dt, rel=1e-12)
+
+
+def test_host_only_mesh_preparation(lib):
+    from workload import psi_sine, square_mesh
+    m = square_mesh(16, box=(0.4, 0.6, 0.4, 0.6), p=4)
+    ctx = lib.lflts_create(-1)
+    try:
+        mid = lib.lflts_mesh_add(ctx, m.xy, m.tri, m.dirichlet, m.P, psi_sine(m, 5))
+        info = lib.lflts_mesh_info(ctx, mid)
+        order = lib.lflts_mesh_order(ctx, mid)
+    finally:
+        lib.lflts_destroy(ctx)
+    free = ~m.dirichlet.astype(bool)
+    P = m.P.astype(bool) & free
+    touch = P[m.tri].any(axis=1)
+    R = np.zeros(m.n_nodes, bool)
+    R[m.tri[touch].ravel()] = True
+    R &= free
+    assert info["n_nodes"] == m.n_nodes and info["n_tri"] == m.n_tri
+    assert info["n_free"] == free.sum() and info["n_P"] == P.sum() and info["n_R"] == R.sum()
+    assert info["K"] == 5 and info["KP"] == 8
+    assert info["n_incidences"] == 3 * m.n_tri - np.isin(m.tri, np.nonzero(~free)[0]).sum()
+    assert sorted(order.tolist()) == list(range(m.n_nodes))
+    nP, nR, nF = info["n_P"], info["n_R"], info["n_free"]
+    assert P[order[:nP]].all()
+    assert R[order[nP:nR]].all() and not P[order[nP:nR]].any()
+    assert free[order[nR:nF]].all() and not R[order[nR:nF]].any()
+    assert not free[order[nF:]].any()
+    # each group keeps the caller's order
+    for a, b in ((0, nP), (nP, nR), (nR, nF), (nF, m.n_nodes)):
+        assert np.all(np.diff(order[a:b]) > 0)
+
+
+def test_invalid_mesh_rejected(lib):
+    ctx = lib.lflts_create(-1)
+    try:
+        xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+        with pytest.raises(lib.LfltsError) as e:
+            lib.lflts_mesh_add(ctx, xy, np.array([[0, 2, 1]]), np.zeros(3), None, np.zeros((1, 1)))
+        assert e.value.code == lib.LFLTS_ERR_MESH
+        with pytest.raises(lib.LfltsError) as e:
+            lib.lflts_mesh_add(ctx, xy, np.array([[0, 1, 3]]), np.zeros(3), None, np.zeros((1, 1)))
+        assert e.value.code == lib.LFLTS_ERR_MESH
+        with pytest.raises(lib.LfltsError):
+            lib.lflts_mesh_add(ctx, xy, np.array([[0, 1, 2]]), np.zeros(3), None, np.zeros((1, 17)))
+    finally:
+        lib.lflts_destroy(ctx)
+
+
+def test_host_only_context_refuses_solves(lib):
+    ctx = lib.lflts_create(-1)
+    try:
+        with pytest.raises(lib.LfltsError) as e:
+            lib.lflts_field_add(ctx, 0, np.zeros(3))
+        assert e.value.code == lib.LFLTS_ERR_ARG
+    finally:
+        lib.lflts_destroy(ctx)
