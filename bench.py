@@ -1,0 +1,442 @@
+"""Benchmark: MLMC level-pair batch of stabilised LF-LTS solves on GB300.
+
+One step = one pass of the whole hot path over the batched workload
+square128-p8-K8-L5-fp32 (5 levels, 128^2 .. 2048^2 base cells, refined box
+8x (p = 8), K = 8 log-field terms, 8192/2048/512/128/32 samples per level as
+fine/coarse pairs on a shared draw): per-sample edge weights, Alg. 2 time
+loop to T = 1 on every mesh, QoI, dQ and FP64 level sums.  Solves on one
+mesh from the two pairs that use it run as one batch, meshes run on
+concurrent streams.
+
+Metric: sample*DOF*substep/s = sum over solves of S * N_steps * (n_free + p*|R|)
+(each free DOF updated once per coarse step plus every DOF of the inner set
+R once per substep) divided by the step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --impl reference the FP64 CPU oracle runs a bounded sample of the same
+workload (level-0 solves of the same draws, one per host core) per step.
+Under torchrun every rank runs the full batch with its own draws (weak
+scaling, no data-path collective); times are maxed over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sample·DOF·substep/s and MLMC time-to-RMSE ε: batched FP32 vs plain FP64"
+UNIT = "sample·DOF·substep/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ----------------------------------------------------------------- helpers
+def _cfg(name):
+    from workload import CONFIG_BANDWIDTH, CONFIG_BATCHED, CONFIG_PLAIN
+    return {"batched": CONFIG_BATCHED, "plain": CONFIG_PLAIN, "bandwidth": CONFIG_BANDWIDTH}[name]
+
+
+def _workload_desc(cfg):
+    return (f"{cfg.name}: unit square, P1 lumped, {cfg.levels} levels with "
+            f"{cfg.n0}^2..{cfg.n0 * 2 ** (cfg.levels - 1)}^2 base cells, box {cfg.box} refined "
+            f"p={cfg.p}, c^2=exp(sum_k xi_k sin(k pi x) sin(k pi y)/k^2) K={cfg.K} xi~U(-1,1), "
+            f"u0=exp(-200|x-(0.3,0.3)|^2), T={cfg.T}, QoI=mean over {cfg.qoi_box}, nu={cfg.nu}, "
+            f"samples {'/'.join(map(str, cfg.samples))} as fine/coarse pairs")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------- CPU oracle
+_ORACLE_LEVEL = {}
+
+
+def _oracle_sample(args):
+    cfg_name, level, xi = args
+    from oracle.lts import solve_qoi
+    from workload import level_problem
+    key = (cfg_name, level)
+    if key not in _ORACLE_LEVEL:
+        _ORACLE_LEVEL[key] = level_problem(_cfg(cfg_name), level)
+    lev = _ORACLE_LEVEL[key]
+    t = time.perf_counter()
+    solve_qoi(lev, xi)
+    return time.perf_counter() - t
+
+
+def oracle_units_per_sample(cfg, level):
+    """Work units of one oracle solve: N_steps * (n_free + p |R|) with R = the
+    vertices of elements touching P (the same count the GPU path reports)."""
+    import numpy as np
+    from workload import level_problem
+    lev = level_problem(cfg, level)
+    m = lev["mesh"]
+    free = ~m.dirichlet.astype(bool)
+    P = m.P.astype(bool) & free
+    R = np.zeros(m.n_nodes, bool)
+    R[m.tri[P[m.tri].any(axis=1)].ravel()] = True
+    R &= free
+    return lev["n_steps"] * (int(free.sum()) + cfg.p * int(R.sum()))
+
+
+class OraclePool:
+    """Spawned worker processes (safe to start after CUDA is initialised)."""
+
+    def __init__(self, cores):
+        import multiprocessing as mp
+        self.cores = cores
+        self.pool = mp.get_context("spawn").Pool(cores)
+
+    def step(self, cfg_name, level, xis):
+        t = time.perf_counter()
+        self.pool.map(_oracle_sample, [(cfg_name, level, x) for x in xis], chunksize=1)
+        return time.perf_counter() - t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(cfg_name, cores, n_rounds=1, pool=None):
+    """Oracle throughput on the host cores: `cores` level-0 samples per round."""
+    from workload import xi_uniform
+    cfg = _cfg(cfg_name)
+    units = oracle_units_per_sample(cfg, 0)
+    own = pool is None
+    pool = pool or OraclePool(cores)
+    try:
+        xis = xi_uniform(cfg.seed, 0, cores * n_rounds, cfg.K)
+        pool.step(cfg_name, 0, xis[:1])  # worker start-up and level build, untimed
+        el = pool.step(cfg_name, 0, list(xis))
+    finally:
+        if own:
+            pool.close()
+    n = cores * n_rounds
+    return {"value": units * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} level-0 solves (128^2 base, p={cfg.p}, {units:.3e} units each) of the "
+                      f"same workload, one per process, FP64 numpy/scipy, {el:.1f} s"}
+
+
+# ------------------------------------------------------------------- GPU
+def setup_gpu(cfg, rank):
+    import numpy as np
+    import torch
+    from paper_2106_11117_gb300 import build, lflts
+    from workload import level_problem, xi_uniform
+    build.build()
+    ctx = lflts.Context(torch.cuda.current_device())
+    hs, levels = [], []
+    for l in range(cfg.levels):
+        lev = level_problem(cfg, l)
+        hs.append(ctx.add_level(lev))
+        levels.append(lev)
+        del lev["mesh"]  # free host memory of large meshes
+    prec = cfg.precision
+    xis_h, xis_d, outs_d, outs_h = [], [], [], []
+    for l, S in enumerate(cfg.samples):
+        x = xi_uniform(cfg.seed + 1000 * rank, l, S, cfg.K)
+        xh = torch.from_numpy(x).pin_memory()
+        xis_h.append(xh)
+        xis_d.append(xh.cuda())
+        outs_d.append([torch.zeros(S, dtype=torch.float64, device="cuda") for _ in range(2)]
+                      + [torch.zeros(4, dtype=torch.float64, device="cuda")])
+        outs_h.append([torch.zeros(S, dtype=torch.float64).pin_memory() for _ in range(2)]
+                      + [torch.zeros(4, dtype=torch.float64).pin_memory()])
+
+    def jobs(device_mem):
+        js = []
+        for l, S in enumerate(cfg.samples):
+            j = lflts.PairJob()
+            j.fine = hs[l].desc(prec)
+            if l > 0:
+                j.coarse = hs[l - 1].desc(prec)
+                j.has_coarse = 1
+            o = outs_d[l] if device_mem else outs_h[l]
+            j.xi = (xis_d[l] if device_mem else xis_h[l]).data_ptr()
+            j.S = S
+            j.dQ, j.Qf, j.sums = o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr()
+            js.append(j)
+        return js
+
+    units = 0
+    solves = {}
+    for l, S in enumerate(cfg.samples):
+        solves[l] = solves.get(l, 0) + S
+        if l > 0:
+            solves[l - 1] = solves.get(l - 1, 0) + S
+    for l, S in solves.items():
+        info = hs[l].info
+        units += S * hs[l].n_steps * (info["n_free"] + cfg.p * info["n_R"])
+    h2d = sum(S * cfg.K * 8 for S in cfg.samples)
+    d2h = sum(S * 8 * 2 + 32 for S in cfg.samples)
+    return {"ctx": ctx, "hs": hs, "jobs_d": jobs(True), "jobs_h": jobs(False), "units": units,
+            "outs_d": outs_d, "outs_h": outs_h, "h2d": h2d, "d2h": d2h, "solves": solves,
+            "lflts": lflts}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    cfg = _cfg(args.config)
+    pool = None
+    if rank == 0 and not args.no_cpu_baseline:
+        pool = OraclePool(args.cpu_cores or os.cpu_count() or 1)
+    W = setup_gpu(cfg, rank)
+    lf = W["lflts"]
+    ctx = W["ctx"]
+    st = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step(device_mem=True):
+        if device_mem:
+            lf.lflts_run_pairs(ctx.h, W["jobs_d"], lf.LFLTS_MEM_DEVICE, st.cuda_stream)
+        else:
+            lf.lflts_run_pairs(ctx.h, W["jobs_h"], lf.LFLTS_MEM_HOST, st.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    lf.lflts_profile_reset(ctx.h)
+    lf.lflts_profile_enable(ctx.h, True)
+    n0 = lf.lflts_launch_count(ctx.h)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = lf.lflts_launch_count(ctx.h) - n0
+    lf.lflts_profile_enable(ctx.h, False)
+    clk = clocks.stop()
+    prof = {k: lf.lflts_profile_read(ctx.h, k) for k in ("init", "coarse", "inner", "qoi", "sums")}
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = W["units"] * world * args.steps / (ms * 1e-3)
+
+    # end to end through the public API with host buffers (copies inside)
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(device_mem=False)
+        torch.cuda.synchronize()
+        barrier()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": W["units"] * world * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": W["h2d"] * world, "d2h_bytes_per_step": W["d2h"] * world}
+
+    # roofline of the dominant kernel class
+    peak, peak_kind = _peaks()
+    dom = max(("coarse", "inner"), key=lambda k: prof[k]["ms"])
+    pd = prof[dom]
+    achieved = pd["alg_bytes"] / (pd["ms"] * 1e-3) / 1e9 if pd["ms"] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": {"coarse": "k_coarse", "inner": "k_inner"}[dom],
+            "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+            "alg_bytes_per_launch": pd["alg_bytes"] / max(pd["launches"], 1),
+            "launches": pd["launches"], "avg_launch_ms": pd["ms"] / max(pd["launches"], 1),
+            "share_of_kernel_time": round(pd["ms"] / sum(v["ms"] for v in prof.values()), 4)}
+
+    cpu = None
+    if pool is not None:
+        cpu = cpu_baseline(args.config, pool.cores, pool=pool)
+        pool.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if cfg.precision == 32 else "f64", "data": "synthetic",
+                "config": {"workload": _workload_desc(cfg),
+                           "solves_per_step": {f"mesh{l}": S for l, S in sorted(W["solves"].items())},
+                           "units_per_step": W["units"] * world,
+                           "l2": "inputs larger than L2 (per-mesh state >= 1 GB), no flush",
+                           "parallelism": f"samples sharded, dp{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk,
+                "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                                       "alg_GBps": round(v["alg_bytes"] / (v["ms"] * 1e-3) / 1e9, 1)
+                                       if v["ms"] > 0 else None} for k, v in prof.items()}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel
+# class, scaled to one launch of this workload (None until captured for the
+# current kernels).
+TRAFFIC_PER_LAUNCH = {}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from workload import xi_uniform
+    cfg = _cfg(args.config)
+    cores = args.cpu_cores or os.cpu_count() or 1
+    units = oracle_units_per_sample(cfg, 0)
+    pool = OraclePool(cores)
+    try:
+        xis = xi_uniform(cfg.seed, 0, cores * (args.warmup + args.steps + 1), cfg.K)
+        pool.step(args.config, 0, xis[:1])
+        k = 0
+        for _ in range(args.warmup):
+            pool.step(args.config, 0, list(xis[k:k + cores]))
+            k += cores
+        el = 0.0
+        for _ in range(args.steps):
+            el += pool.step(args.config, 0, list(xis[k:k + cores]))
+            k += cores
+    finally:
+        pool.close()
+    value = units * cores * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": _workload_desc(cfg),
+                       "sample": f"each step: {cores} level-0 solves (one per host core)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{cores} level-0 solves per step, {args.steps} timed steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_profile_case(args):
+    """Small case for ncu captures: a few steps of one batched FP32 mesh solve
+    with the benchmark's launch configuration (level args.profile_case)."""
+    import torch
+    from paper_2106_11117_gb300 import build, lflts
+    from workload import level_problem, xi_uniform
+    build.build()
+    cfg = _cfg(args.config)
+    l = args.profile_case
+    S = cfg.samples[l] + (cfg.samples[l + 1] if l + 1 < cfg.levels else 0)
+    if args.profile_samples:
+        S = args.profile_samples
+    ctx = lflts.Context(0)
+    h = ctx.add_level(level_problem(cfg, l))
+    xi = torch.from_numpy(xi_uniform(cfg.seed, l, S, cfg.K)).cuda()
+    Q = torch.zeros(S, dtype=torch.float64, device="cuda")
+    d = h.desc(cfg.precision)
+    d.n_steps = args.profile_steps
+    lflts.lflts_solve(ctx.h, d, xi, S, Q, None, lflts.LFLTS_MEM_DEVICE, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    info = h.info
+    print(json.dumps({"profile_case": f"{cfg.name} level {l}", "S": S, "n_steps": d.n_steps, **info}))
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=["batched", "plain", "bandwidth"], default="batched")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-cores", type=int, default=0)
+    ap.add_argument("--profile-case", type=int, default=-1,
+                    help="run only a few steps of one mesh solve (for ncu captures)")
+    ap.add_argument("--profile-steps", type=int, default=4)
+    ap.add_argument("--profile-samples", type=int, default=0)
+    args = ap.parse_args()
+    if args.profile_case >= 0:
+        run_profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -101,7 +101,8 @@ int lflts_mesh_add(lflts_ctx* ctx, const double* xy, int64_t n_nodes,
 /*
  * Sizes of a registered mesh: info[0] n_nodes, [1] n_free (non-Dirichlet),
  * [2] n_R (nodes the inner substeps update: P and its element neighbours),
- * [3] n_P, [4] n_tri, [5] K, [6] number of node-element incidences.
+ * [3] n_P, [4] n_tri, [5] K, [6] n_edges (edges with a nonzero stiffness
+ * entry and a free endpoint), [7] n_edges_P (those with an endpoint in P).
  */
 int lflts_mesh_info(lflts_ctx* ctx, int mesh_id, int64_t info[8]);
 

@@ -16,137 +16,233 @@
 // (start value z_1 = q_1(z_0) + dt M^{1/2} v0).  A node outside R (no P node
 // in any incident element) has a(P r_m) = 0, so its r_p = -gamma g with the
 // scalar gamma of the same recursion (gamma = dt^2 / 2: Alg. 2 is leapfrog
-// away from the refined region, Sec. 3.3).
+// away from the refined region, Sec. 3.3).  r_1 is never stored: it is
+// -c_0 g wherever it is needed.
 //
-// Layout: sample-major state [node][S]; the thread (node i, sample s) reads
-// neighbours at [j][s], so a warp over 32 consecutive samples of one node
-// issues one 128-byte transaction per neighbour.  Element coefficients are
-// recomputed in registers: c_e^2 = exp2(sum_k xi_k psi2[e][k]) with psi2
-// pre-scaled by log2(e).
+// Stiffness in edge form: (K u)_i = sum_{j ~ i} K_ij(w) (u_j - u_i) with the
+// per-sample edge weights K_ij(w) = sum_e c_e^2(w) G_e[i][j] evaluated once per
+// solve (the random field at the element quadrature points, Sec. 3.2: its
+// cost is a lower-order term) and stored sample-major [edge][S].
+//
+// Layout: every per-node and per-edge array is sample-major [index][S]; a
+// thread owns VEC consecutive samples of one node (float4 / double2 loads), a
+// group of SB threads covers SB*VEC consecutive samples of that node, so
+// neighbour reads are contiguous 128..512-byte segments.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
 
 namespace lflts {
 
-template <typename Real> struct Vec2T;
-template <> struct Vec2T<float> { using type = float2; };
-template <> struct Vec2T<double> { using type = double2; };
-
 template <typename Real>
 struct MeshDev {
   int n_free, n_R, n_P;
-  const int* __restrict__ inc_ptr;                       // [n_free + 1]
-  const int4* __restrict__ inc;                          // (e, j1, j2, 0)
-  const typename Vec2T<Real>::type* __restrict__ w;      // (G_i,j1, G_i,j2)
-  const Real* __restrict__ minv;                         // [n_free]
-  const Real* __restrict__ psi2;                         // [n_tri][KP]
+  const int* __restrict__ adj_ptr;   // [n_free + 1]
+  const int2* __restrict__ adj;      // (neighbour, edge)
+  const Real* __restrict__ minv;     // [n_free]
 };
+
+// --- vector access of VEC consecutive samples -------------------------------
+template <typename Real, int V>
+struct Pack {
+  Real v[V];
+};
+
+template <typename Real, int V>
+__device__ __forceinline__ Pack<Real, V> ldp(const Real* __restrict__ p) {
+  Pack<Real, V> r;
+  if constexpr (V == 4 && sizeof(Real) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else if constexpr (V == 2 && sizeof(Real) == 8) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    r.v[0] = t.x; r.v[1] = t.y;
+  } else if constexpr (V == 2 && sizeof(Real) == 4) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    r.v[0] = t.x; r.v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) r.v[k] = p[k];
+  }
+  return r;
+}
+
+template <typename Real, int V>
+__device__ __forceinline__ void stp(Real* __restrict__ p, const Pack<Real, V>& r) {
+  if constexpr (V == 4 && sizeof(Real) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  } else if constexpr (V == 2 && sizeof(Real) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
+  } else if constexpr (V == 2 && sizeof(Real) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(r.v[0], r.v[1]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) p[k] = r.v[k];
+  }
+}
 
 __device__ __forceinline__ float exp2_r(float x) { return exp2f(x); }
 __device__ __forceinline__ double exp2_r(double x) { return exp2(x); }
 
-// c_e^2 for the draw held in registers.
-template <typename Real, int KP>
-__device__ __forceinline__ Real coef(const Real (&xr)[KP], const Real* __restrict__ pe) {
-  Real acc = Real(0);
-#pragma unroll
-  for (int k = 0; k < KP; ++k) acc = fma(xr[k], __ldg(pe + k), acc);
-  return exp2_r(acc);
-}
-
-template <typename Real, int KP>
-__device__ __forceinline__ void load_xi(Real (&xr)[KP], const Real* __restrict__ xi, int s) {
-#pragma unroll
-  for (int k = 0; k < KP; ++k) xr[k] = xi[(size_t)s * KP + k];
+// Thread -> (node row, sample vector) for blockDim.x = 256 threads.
+struct Lane {
+  int sv;   // sample-vector index (samples sv*VEC .. sv*VEC+VEC-1)
+  int row;  // node row within the block
+  int NB;   // node rows per block
+};
+__device__ __forceinline__ Lane lane_of(int SB) {
+  Lane l;
+  l.sv = blockIdx.y * SB + (threadIdx.x & (SB - 1));
+  l.NB = blockDim.x / SB;
+  l.row = threadIdx.x / SB;
+  return l;
 }
 
 // ---------------------------------------------------------------------------
-// Coarse part of one step, all free nodes: g = a(u_n).
-//   outside R: d += -kappa*gamma*g, u_next = u_n + d
-//   inside  R: store g and r_1 = -c0 g
-// Thread layout: blockDim.x = 256 = SB samples x (256/SB) node rows.
+// Per-sample edge weights K_ij(w) = sum_e exp2(xi . psi2[e]) G_e[i][j].
+// One thread per (edge, sample).  Once per solve.
 // ---------------------------------------------------------------------------
 template <typename Real, int KP>
 __global__ void __launch_bounds__(256)
-k_coarse(MeshDev<Real> m, const Real* __restrict__ xi, int S, int SB,
-         const Real* __restrict__ u, Real* __restrict__ u_next, Real* __restrict__ d,
-         Real* __restrict__ g, Real* __restrict__ r1, Real kappa_gamma, Real c0) {
+k_edge_weights(int64_t n_edges, int S, int SB, const int2* __restrict__ ee,
+               const Real* __restrict__ eg, const Real* __restrict__ psi2,
+               const Real* __restrict__ xi, Real* __restrict__ W) {
   const int ls = threadIdx.x & (SB - 1);
   const int NB = blockDim.x / SB;
-  const int ln = threadIdx.x / SB;
   const int s = blockIdx.y * SB + ls;
   if (s >= S) return;
   Real xr[KP];
-  load_xi<Real, KP>(xr, xi, s);
-  for (int i = blockIdx.x * NB + ln; i < m.n_free; i += gridDim.x * NB) {
-    const size_t is = (size_t)i * S + s;
-    const Real ui = u[is];
-    Real acc = Real(0);
-    const int t1 = m.inc_ptr[i + 1];
-    for (int t = m.inc_ptr[i]; t < t1; ++t) {
-      const int4 ie = m.inc[t];
-      const auto w = m.w[t];
-      const Real c2 = coef<Real, KP>(xr, m.psi2 + (size_t)ie.x * KP);
-      const Real u1 = u[(size_t)ie.y * S + s];
-      const Real u2 = u[(size_t)ie.z * S + s];
-      acc = fma(c2, w.x * (u1 - ui) + w.y * (u2 - ui), acc);
+#pragma unroll
+  for (int k = 0; k < KP; ++k) xr[k] = xi[(size_t)s * KP + k];
+  for (int64_t e = (int64_t)blockIdx.x * NB + threadIdx.x / SB; e < n_edges; e += (int64_t)gridDim.x * NB) {
+    const int2 el = ee[e];
+    Real w = Real(0);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int t = side ? el.y : el.x;
+      if (t < 0) continue;
+      const Real* pe = psi2 + (size_t)t * KP;
+      Real acc = Real(0);
+#pragma unroll
+      for (int k = 0; k < KP; ++k) acc = fma(xr[k], __ldg(pe + k), acc);
+      w = fma(exp2_r(acc), eg[2 * e + side], w);
     }
-    const Real gi = m.minv[i] * acc;
+    W[(size_t)e * S + s] = w;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coarse part of one step, all free nodes: g = a(u_n) = M^-1 K u_n.
+//   outside R: d += -kappa*gamma*g, u_next = u_n + d
+//   inside  R: store g
+// ---------------------------------------------------------------------------
+template <typename Real, int VEC>
+__global__ void __launch_bounds__(256)
+k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real* __restrict__ u,
+         Real* __restrict__ u_next, Real* __restrict__ d, Real* __restrict__ g, Real kappa_gamma) {
+  const Lane l = lane_of(SB);
+  const int s0 = l.sv * VEC;
+  if (s0 >= S) return;
+  for (int i = blockIdx.x * l.NB + l.row; i < m.n_free; i += gridDim.x * l.NB) {
+    const size_t is = (size_t)i * S + s0;
+    const Pack<Real, VEC> ui = ldp<Real, VEC>(u + is);
+    Real acc[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) acc[k] = Real(0);
+    const int t1 = m.adj_ptr[i + 1];
+    for (int t = m.adj_ptr[i]; t < t1; ++t) {
+      const int2 nb = m.adj[t];
+      const Pack<Real, VEC> uj = ldp<Real, VEC>(u + (size_t)nb.x * S + s0);
+      const Pack<Real, VEC> w = ldp<Real, VEC>(W + (size_t)nb.y * S + s0);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) acc[k] = fma(w.v[k], uj.v[k] - ui.v[k], acc[k]);
+    }
+    const Real mi = m.minv[i];
+    Pack<Real, VEC> gi;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) gi.v[k] = mi * acc[k];
     if (i >= m.n_R) {
-      const Real dn = d[is] - kappa_gamma * gi;
-      d[is] = dn;
-      u_next[is] = ui + dn;
+      Pack<Real, VEC> dn = ldp<Real, VEC>(d + is), un;
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) {
+        dn.v[k] = dn.v[k] - kappa_gamma * gi.v[k];
+        un.v[k] = ui.v[k] + dn.v[k];
+      }
+      stp<Real, VEC>(d + is, dn);
+      stp<Real, VEC>(u_next + is, un);
     } else {
-      g[is] = gi;
-      r1[is] = -c0 * gi;
+      stp<Real, VEC>(g + is, gi);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// One inner substep m on R:  r_{m+1} = (1+beta) r_m - beta r_{m-1} - cm (g + a(P r_m)).
-// FIRST: r_{m-1} = r_0 = 0.  LAST: fold r_p into d and u_next instead of storing it.
+// One inner substep m on R:
+//   r_{m+1} = (1+beta) r_m - beta r_{m-1} - cm (g + a(P r_m)),
+// r_m = s_cur * cur, r_{m-1} = s_prev * prev (prev == nullptr: r_0 = 0).
+// LAST: fold r_p into d and u_next instead of storing it.
 // ---------------------------------------------------------------------------
-template <typename Real, int KP, bool FIRST, bool LAST>
+template <typename Real, int VEC, bool LAST>
 __global__ void __launch_bounds__(256)
-k_inner(MeshDev<Real> m, const Real* __restrict__ xi, int S, int SB,
-        const Real* __restrict__ r_cur, const Real* __restrict__ r_prev, Real* __restrict__ r_next,
-        const Real* __restrict__ g, const Real* __restrict__ u, Real* __restrict__ u_next,
-        Real* __restrict__ d, Real one_plus_beta, Real beta, Real cm, Real kappa) {
-  const int ls = threadIdx.x & (SB - 1);
-  const int NB = blockDim.x / SB;
-  const int ln = threadIdx.x / SB;
-  const int s = blockIdx.y * SB + ls;
-  if (s >= S) return;
-  Real xr[KP];
-  load_xi<Real, KP>(xr, xi, s);
+k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
+        const Real* __restrict__ cur, Real s_cur, const Real* __restrict__ prev, Real s_prev,
+        Real* __restrict__ r_next, const Real* __restrict__ g, const Real* __restrict__ u,
+        Real* __restrict__ u_next, Real* __restrict__ d, Real one_plus_beta, Real beta, Real cm,
+        Real kappa) {
+  const Lane l = lane_of(SB);
+  const int s0 = l.sv * VEC;
+  if (s0 >= S) return;
   const int nP = m.n_P;
-  for (int i = blockIdx.x * NB + ln; i < m.n_R; i += gridDim.x * NB) {
-    const size_t is = (size_t)i * S + s;
-    const Real rc = r_cur[is];
+  for (int i = blockIdx.x * l.NB + l.row; i < m.n_R; i += gridDim.x * l.NB) {
+    const size_t is = (size_t)i * S + s0;
     const bool iP = i < nP;
-    const Real vi = iP ? rc : Real(0);
-    Real acc = Real(0);
-    const int t1 = m.inc_ptr[i + 1];
-    for (int t = m.inc_ptr[i]; t < t1; ++t) {
-      const int4 ie = m.inc[t];
-      const bool p1 = ie.y < nP, p2 = ie.z < nP;
-      if (!(iP || p1 || p2)) continue;  // element without P vertex: no AP term
-      const auto w = m.w[t];
-      const Real c2 = coef<Real, KP>(xr, m.psi2 + (size_t)ie.x * KP);
-      const Real v1 = p1 ? r_cur[(size_t)ie.y * S + s] : Real(0);
-      const Real v2 = p2 ? r_cur[(size_t)ie.z * S + s] : Real(0);
-      acc = fma(c2, w.x * (v1 - vi) + w.y * (v2 - vi), acc);
+    const Pack<Real, VEC> rc = ldp<Real, VEC>(cur + is);
+    Real vi[VEC], acc[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      vi[k] = iP ? s_cur * rc.v[k] : Real(0);
+      acc[k] = Real(0);
     }
-    const Real rp = FIRST ? Real(0) : r_prev[is];
-    const Real rn = one_plus_beta * rc - beta * rp - cm * (g[is] + m.minv[i] * acc);
-    if (LAST) {
-      const Real dn = d[is] + kappa * rn;
-      d[is] = dn;
-      u_next[is] = u[is] + dn;
+    const int t1 = m.adj_ptr[i + 1];
+    for (int t = m.adj_ptr[i]; t < t1; ++t) {
+      const int2 nb = m.adj[t];
+      const bool jP = nb.x < nP;
+      if (!jP && !iP) break;  // neighbours sorted: no P neighbour left
+      const Pack<Real, VEC> w = ldp<Real, VEC>(W + (size_t)nb.y * S + s0);
+      if (jP) {
+        const Pack<Real, VEC> rj = ldp<Real, VEC>(cur + (size_t)nb.x * S + s0);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) acc[k] = fma(w.v[k], s_cur * rj.v[k] - vi[k], acc[k]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) acc[k] = fma(w.v[k], -vi[k], acc[k]);
+      }
+    }
+    const Real mi = m.minv[i];
+    const Pack<Real, VEC> gi = ldp<Real, VEC>(g + is);
+    Pack<Real, VEC> rp;
+    if (prev) {
+      rp = ldp<Real, VEC>(prev + is);
     } else {
-      r_next[is] = rn;
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) rp.v[k] = Real(0);
+    }
+    Pack<Real, VEC> rn;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k)
+      rn.v[k] = one_plus_beta * (s_cur * rc.v[k]) - beta * (s_prev * rp.v[k]) - cm * (gi.v[k] + mi * acc[k]);
+    if (LAST) {
+      const Pack<Real, VEC> ui = ldp<Real, VEC>(u + is);
+      Pack<Real, VEC> dn = ldp<Real, VEC>(d + is), un;
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) {
+        dn.v[k] = dn.v[k] + kappa * rn.v[k];
+        un.v[k] = ui.v[k] + dn.v[k];
+      }
+      stp<Real, VEC>(d + is, dn);
+      stp<Real, VEC>(u_next + is, un);
+    } else {
+      stp<Real, VEC>(r_next + is, rn);
     }
   }
 }

@@ -34,10 +34,11 @@ struct Buf {
 
 struct MeshGPU {
   HostMesh h;
-  int* inc_ptr = nullptr;
-  int4* inc = nullptr;
-  float2* w32 = nullptr;
-  double2* w64 = nullptr;
+  int* adj_ptr = nullptr;
+  int2* adj = nullptr;
+  int2* ee = nullptr;       // elements of each edge
+  float* eg32 = nullptr;    // [n_edges][2] element entries G
+  double* eg64 = nullptr;
   float* minv32 = nullptr;
   double* minv64 = nullptr;
   float* psi32 = nullptr;
@@ -59,7 +60,7 @@ struct Qoi {
 };
 
 struct Workspace {
-  Buf ua, ub, d, g, r0, r1, r2, xipad, xraw, qps, qpc, Q, uN;
+  Buf ua, ub, d, g, r0, r1, r2, W, xipad, xraw, qps, qpc, Q, uN;
 };
 
 struct ProfRec {
@@ -209,11 +210,22 @@ struct Geo {
   int SB;
 };
 
-Geo geometry(const lflts_ctx* c, int64_t n, int64_t S) {
+// Launch shape of the node/edge kernels: SB lanes per node (a power of two
+// up to 32) each owning one sample vector.  Grid x covers the nodes
+// (grid-stride), grid y the sample slabs; about 16 CTAs of 256 threads per SM.
+// SB is the largest lane count that leaves at most a quarter of the lanes of
+// the sample slabs idle.
+Geo geometry(const lflts_ctx* c, int64_t n, int64_t SV) {
   int SB = 1;
-  while (SB < 32 && SB * 2 <= S) SB *= 2;
+  for (int sb = 32; sb > 1; sb /= 2) {
+    const int64_t waste = ((SV + sb - 1) / sb) * sb - SV;
+    if (waste * 4 <= SV) {
+      SB = sb;
+      break;
+    }
+  }
   const int NB = 256 / SB;
-  const int64_t gy = (S + SB - 1) / SB;
+  const int64_t gy = (SV + SB - 1) / SB;
   const int64_t target = int64_t(c->sms) * 16;
   int64_t gx = std::max<int64_t>(1, std::min<int64_t>((n + NB - 1) / NB, std::max<int64_t>(1, target / gy)));
   Geo g;
@@ -232,17 +244,97 @@ struct Sel;
 template <>
 struct Sel<float> {
   static MeshDev<float> mesh(const MeshGPU& m, int n_R) {
-    return MeshDev<float>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.inc_ptr, m.inc, m.w32, m.minv32, m.psi32};
+    return MeshDev<float>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.adj_ptr, m.adj, m.minv32};
   }
   static const float* field(const Field& f) { return f.v32; }
+  static const float* eg(const MeshGPU& m) { return m.eg32; }
+  static const float* psi(const MeshGPU& m) { return m.psi32; }
 };
 template <>
 struct Sel<double> {
   static MeshDev<double> mesh(const MeshGPU& m, int n_R) {
-    return MeshDev<double>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.inc_ptr, m.inc, m.w64, m.minv64, m.psi64};
+    return MeshDev<double>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.adj_ptr, m.adj, m.minv64};
   }
   static const double* field(const Field& f) { return f.v64; }
+  static const double* eg(const MeshGPU& m) { return m.eg64; }
+  static const double* psi(const MeshGPU& m) { return m.psi64; }
 };
+
+// Geometry of the node/edge kernels: SB lanes of VEC samples per node.
+Geo geometry_vec(const lflts_ctx* c, int64_t n, int64_t S, int vec) {
+  return geometry(c, n, S / vec);
+}
+
+// The time loop of Alg. 2 for one batch (see kernels.cuh for the u-form).
+template <typename Real, int VEC>
+int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S,
+              Workspace& ws, Real*& uc_out, cudaStream_t st) {
+  const HostMesh& h = mg.h;
+  const size_t rb = sizeof(Real);
+  const int p = ds.p;
+  Real* ua = static_cast<Real*>(ws.ua.p);
+  Real* ub = static_cast<Real*>(ws.ub.p);
+  Real* d = static_cast<Real*>(ws.d.p);
+  Real* g = static_cast<Real*>(ws.g.p);
+  Real* rbuf[3] = {static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p)};
+  const Real* W = static_cast<const Real*>(ws.W.p);
+
+  std::vector<double> beta, cm;
+  double delta, omega, c0, gamma;
+  lts_constants(p, ds.nu, ds.dt, beta, cm, delta, omega, c0, gamma);
+  const MeshDev<Real> md = Sel<Real>::mesh(mg, n_R);
+  const Geo gc = geometry_vec(c, h.n_free, S, VEC);
+  const Geo gi = geometry_vec(c, std::max(n_R, 1), S, VEC);
+  const double Srb = double(S) * rb;
+  const double coarse_bytes = Srb * (4.0 * h.n_free - 2.0 * n_R + double(h.n_edges));
+  const double edgeP_bytes = Srb * double(h.n_edges_P);
+
+  Real* uc = ua;
+  Real* un = ub;
+  for (int64_t n = 0; n < ds.n_steps; ++n) {
+    const Real kappa = (n == 0) ? Real(1) : Real(2);
+    {
+      Prof pr(c, st);
+      k_coarse<Real, VEC><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g,
+                                                    (Real)(double(kappa) * gamma));
+      LF_CUDA(c, cudaGetLastError());
+      pr.end(LFLTS_KERNEL_COARSE, coarse_bytes);
+    }
+    if (n_R > 0) {
+      // r_1 = -c0 g is read from g; r_2.. rotate through three buffers
+      const Real* cur = g;
+      Real s_cur = (Real)(-c0);
+      const Real* prev = nullptr;
+      Real s_prev = Real(0);
+      int nxt = 0;
+      for (int m = 1; m < p; ++m) {
+        const bool last = (m == p - 1);
+        const Real opb = (Real)(1.0 + beta[m]), bt = (Real)beta[m], cmm = (Real)cm[m];
+        Real* rn = rbuf[nxt];
+        Prof pr(c, st);
+        if (last)
+          k_inner<Real, VEC, true><<<gi.grid, 256, 0, st>>>(md, (int)S, gi.SB, W, cur, s_cur, prev, s_prev, rn, g,
+                                                            uc, un, d, opb, bt, cmm, kappa);
+        else
+          k_inner<Real, VEC, false><<<gi.grid, 256, 0, st>>>(md, (int)S, gi.SB, W, cur, s_cur, prev, s_prev, rn, g,
+                                                             uc, un, d, opb, bt, cmm, kappa);
+        LF_CUDA(c, cudaGetLastError());
+        // values per R node: cur, prev (unless it is g), g, the new r (or d, u in, d, u out)
+        const double reads = (m == 1 ? 1.0 : (m == 2 ? 2.0 : 3.0));
+        const double per_node = reads + (last ? 4.0 : 1.0);
+        pr.end(LFLTS_KERNEL_INNER, per_node * n_R * Srb + edgeP_bytes);
+        prev = cur;
+        s_prev = s_cur;
+        cur = rn;
+        s_cur = Real(1);
+        nxt = (nxt + 1) % 3;
+      }
+    }
+    std::swap(uc, un);
+  }
+  uc_out = uc;
+  return 0;
+}
 
 template <typename Real, int KP>
 int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, const Qoi& q,
@@ -262,69 +354,37 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, co
   LF_TRY(ensure(c, ws.r0, r_bytes));
   LF_TRY(ensure(c, ws.r1, r_bytes));
   LF_TRY(ensure(c, ws.r2, r_bytes));
+  LF_TRY(ensure(c, ws.W, size_t(std::max<int64_t>(h.n_edges, 1)) * S * rb));
   LF_TRY(ensure(c, ws.xipad, size_t(S) * KP * rb));
   Real* ua = static_cast<Real*>(ws.ua.p);
   Real* ub = static_cast<Real*>(ws.ub.p);
   Real* d = static_cast<Real*>(ws.d.p);
-  Real* g = static_cast<Real*>(ws.g.p);
-  Real* rbuf[3] = {static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p)};
   Real* xi = static_cast<Real*>(ws.xipad.p);
+  Real* W = static_cast<Real*>(ws.W.p);
 
-  {
+  {  // a1: draws, initial state, per-sample edge weights of K(w)
     Prof pr(c, st);
     k_xi_pad<Real, KP><<<blocks_for(S * KP, 256, 4096), 256, 0, st>>>((int)S, h.K, d_xi, xi);
     LF_CUDA(c, cudaGetLastError());
     k_init_state<Real><<<blocks_for(n_nodes * S, 256, c->sms * 32), 256, 0, st>>>(
         n_nodes, (int)S, Sel<Real>::field(u0), v0 ? Sel<Real>::field(*v0) : nullptr, (Real)ds.dt, ua, ub, d);
     LF_CUDA(c, cudaGetLastError());
-    pr.end(LFLTS_KERNEL_INIT, double(n_nodes) * S * rb * 3);
-    c->launches++;  // two kernels in this class
+    const Geo ge = geometry(c, std::max<int64_t>(h.n_edges, 1), S);
+    k_edge_weights<Real, KP><<<ge.grid, 256, 0, st>>>(h.n_edges, (int)S, ge.SB, mg.ee, Sel<Real>::eg(mg),
+                                                      Sel<Real>::psi(mg), xi, W);
+    LF_CUDA(c, cudaGetLastError());
+    pr.end(LFLTS_KERNEL_INIT, double(S) * rb * (3.0 * n_nodes + double(h.n_edges)));
+    c->launches += 2;  // three kernels in this class
   }
 
-  std::vector<double> beta, cm;
-  double delta, omega, c0, gamma;
-  lts_constants(p, ds.nu, ds.dt, beta, cm, delta, omega, c0, gamma);
-  const MeshDev<Real> md = Sel<Real>::mesh(mg, n_R);
-  const Geo gc = geometry(c, h.n_free, S);
-  const Geo gi = geometry(c, std::max(n_R, 1), S);
-  const double coarse_bytes = double(S) * rb * (4.0 * h.n_free - n_R);
-
-  Real* uc = ua;
-  Real* un = ub;
-  for (int64_t n = 0; n < ds.n_steps; ++n) {
-    const Real kappa = (n == 0) ? Real(1) : Real(2);
-    {
-      Prof pr(c, st);
-      k_coarse<Real, KP><<<gc.grid, 256, 0, st>>>(md, xi, (int)S, gc.SB, uc, un, d, g, rbuf[0],
-                                                   (Real)(double(kappa) * gamma), (Real)c0);
-      LF_CUDA(c, cudaGetLastError());
-      pr.end(LFLTS_KERNEL_COARSE, coarse_bytes);
-    }
-    if (n_R > 0) {
-      int cur = 0, prev = -1;
-      for (int m = 1; m < p; ++m) {
-        const int nxt = (cur + 1) % 3 == prev ? (cur + 2) % 3 : (cur + 1) % 3;
-        const bool first = (m == 1), last = (m == p - 1);
-        const Real* rp = prev >= 0 ? rbuf[prev] : nullptr;
-        const Real opb = (Real)(1.0 + beta[m]), bt = (Real)beta[m], cmm = (Real)cm[m];
-        Prof pr(c, st);
-        if (first && last)
-          k_inner<Real, KP, true, true><<<gi.grid, 256, 0, st>>>(md, xi, (int)S, gi.SB, rbuf[cur], rp, rbuf[nxt], g, uc, un, d, opb, bt, cmm, kappa);
-        else if (first)
-          k_inner<Real, KP, true, false><<<gi.grid, 256, 0, st>>>(md, xi, (int)S, gi.SB, rbuf[cur], rp, rbuf[nxt], g, uc, un, d, opb, bt, cmm, kappa);
-        else if (last)
-          k_inner<Real, KP, false, true><<<gi.grid, 256, 0, st>>>(md, xi, (int)S, gi.SB, rbuf[cur], rp, rbuf[nxt], g, uc, un, d, opb, bt, cmm, kappa);
-        else
-          k_inner<Real, KP, false, false><<<gi.grid, 256, 0, st>>>(md, xi, (int)S, gi.SB, rbuf[cur], rp, rbuf[nxt], g, uc, un, d, opb, bt, cmm, kappa);
-        LF_CUDA(c, cudaGetLastError());
-        const double per_node = last ? (first ? 6.0 : 7.0) : (first ? 3.0 : 4.0);
-        pr.end(LFLTS_KERNEL_INNER, per_node * n_R * double(S) * rb);
-        prev = cur;
-        cur = nxt;
-      }
-    }
-    std::swap(uc, un);
-  }
+  Real* uc = nullptr;
+  const int vmax = (sizeof(Real) == 4) ? 4 : 2;
+  int vec = 1;
+  if (S % vmax == 0) vec = vmax;
+  else if (S % 2 == 0) vec = 2;
+  if (vec == 4) LF_TRY((time_loop<Real, 4>(c, ds, mg, n_R, S, ws, uc, st)));
+  else if (vec == 2) LF_TRY((time_loop<Real, 2>(c, ds, mg, n_R, S, ws, uc, st)));
+  else LF_TRY((time_loop<Real, 1>(c, ds, mg, n_R, S, ws, uc, st)));
 
   // QoI at t_N (Sec. 2.1), FP64 compensated accumulation.
   {
@@ -441,7 +501,7 @@ int lflts_destroy(lflts_ctx* c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     for (auto& w : c->ws)
-      for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->xipad, &w->xraw, &w->qps,
+      for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->W, &w->xipad, &w->xraw, &w->qps,
                      &w->qpc, &w->Q, &w->uN})
         if (b->p) cudaFree(b->p);
     for (void* p : c->owned) cudaFree(p);
@@ -471,21 +531,23 @@ int lflts_mesh_add(lflts_ctx* c, const double* xy, int64_t n_nodes, const int32_
   if (c->device >= 0) {
     LF_TRY(set_device(c));
     const HostMesh& h = mg->h;
-    const size_t ni = h.inc_e.size();
-    std::vector<int4> inc(ni);
-    std::vector<float2> w32(ni);
-    std::vector<double2> w64(ni);
-    for (size_t t = 0; t < ni; ++t) {
-      inc[t] = make_int4(h.inc_e[t], h.inc_j1[t], h.inc_j2[t], 0);
-      w32[t] = make_float2((float)h.inc_w1[t], (float)h.inc_w2[t]);
-      w64[t] = make_double2(h.inc_w1[t], h.inc_w2[t]);
+    const size_t na = h.adj_j.size(), ne = static_cast<size_t>(h.n_edges);
+    std::vector<int2> adj(na), ee(ne);
+    for (size_t t = 0; t < na; ++t) adj[t] = make_int2(h.adj_j[t], h.adj_e[t]);
+    std::vector<double> eg64(2 * ne);
+    for (size_t k = 0; k < ne; ++k) {
+      ee[k] = make_int2(h.edge_e0[k], h.edge_e1[k]);
+      eg64[2 * k] = h.edge_G0[k];
+      eg64[2 * k + 1] = h.edge_G1[k];
     }
+    std::vector<float> eg32(eg64.begin(), eg64.end());
     std::vector<float> minv32(h.minv.begin(), h.minv.end());
     std::vector<float> psi32(h.psi2.begin(), h.psi2.end());
-    LF_TRY(upload(c, &mg->inc_ptr, h.inc_ptr.data(), h.inc_ptr.size()));
-    LF_TRY(upload(c, &mg->inc, inc.data(), ni));
-    LF_TRY(upload(c, &mg->w32, w32.data(), ni));
-    LF_TRY(upload(c, &mg->w64, w64.data(), ni));
+    LF_TRY(upload(c, &mg->adj_ptr, h.adj_ptr.data(), h.adj_ptr.size()));
+    LF_TRY(upload(c, &mg->adj, adj.data(), na));
+    LF_TRY(upload(c, &mg->ee, ee.data(), ne));
+    LF_TRY(upload(c, &mg->eg32, eg32.data(), eg32.size()));
+    LF_TRY(upload(c, &mg->eg64, eg64.data(), eg64.size()));
     LF_TRY(upload(c, &mg->minv32, minv32.data(), minv32.size()));
     LF_TRY(upload(c, &mg->minv64, h.minv.data(), h.minv.size()));
     LF_TRY(upload(c, &mg->psi32, psi32.data(), psi32.size()));
@@ -507,8 +569,8 @@ int lflts_mesh_info(lflts_ctx* c, int mesh_id, int64_t info[8]) {
   info[3] = h.n_P;
   info[4] = h.n_tri;
   info[5] = h.K;
-  info[6] = static_cast<int64_t>(h.inc_e.size());
-  info[7] = h.KP;
+  info[6] = h.n_edges;
+  info[7] = h.n_edges_P;
   return LFLTS_OK;
 }
 

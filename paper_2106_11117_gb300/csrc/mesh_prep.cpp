@@ -106,23 +106,13 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
   m.minv.assign(m.n_free, 0.0);
   for (int64_t k = 0; k < m.n_free; ++k) m.minv[k] = 1.0 / mass[m.new2old[k]];
 
-  // ---- incidences of free nodes -------------------------------------------
-  std::vector<int32_t> count(m.n_free + 1, 0);
-  for (int64_t e = 0; e < n_tri; ++e)
-    for (int a = 0; a < 3; ++a) {
-      const int32_t nn = m.old2new[tri[3 * e + a]];
-      if (nn < m.n_free) count[nn + 1]++;
-    }
-  m.inc_ptr.assign(m.n_free + 1, 0);
-  for (int64_t k = 0; k < m.n_free; ++k) m.inc_ptr[k + 1] = m.inc_ptr[k] + count[k + 1];
-  const int64_t n_inc = m.inc_ptr[m.n_free];
-  m.inc_e.assign(n_inc, 0);
-  m.inc_j1.assign(n_inc, 0);
-  m.inc_j2.assign(n_inc, 0);
-  m.inc_w1.assign(n_inc, 0.0);
-  m.inc_w2.assign(n_inc, 0.0);
-  std::vector<int32_t> fill(m.inc_ptr.begin(), m.inc_ptr.end() - 1);
-  // visit elements in the new element order so each node's list is sorted
+  // ---- edges: (lo, hi, element, G) records grouped by edge ---------------
+  struct Rec {
+    int32_t lo, hi, e;
+    double G;
+  };
+  std::vector<Rec> rec;
+  rec.reserve(static_cast<size_t>(n_tri) * 3);
   for (int64_t k = 0; k < n_tri; ++k) {
     const int64_t e = eorder[k];
     const int32_t* v = tri + 3 * e;
@@ -134,15 +124,73 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
     }
     const double inv4A = 1.0 / (2.0 * area2[e]);  // 1 / (4 |T|)
     for (int a = 0; a < 3; ++a) {
-      const int32_t nn = m.old2new[v[a]];
-      if (nn >= m.n_free) continue;
-      const int b = (a + 1) % 3, c = (a + 2) % 3;
-      const int32_t t = fill[nn]++;
-      m.inc_e[t] = static_cast<int32_t>(k);
-      m.inc_j1[t] = m.old2new[v[b]];
-      m.inc_j2[t] = m.old2new[v[c]];
-      m.inc_w1[t] = (E[a][0] * E[b][0] + E[a][1] * E[b][1]) * inv4A;
-      m.inc_w2[t] = (E[a][0] * E[c][0] + E[a][1] * E[c][1]) * inv4A;
+      const int b = (a + 1) % 3;
+      const int32_t i = m.old2new[v[a]], j = m.old2new[v[b]];
+      const double G = (E[a][0] * E[b][0] + E[a][1] * E[b][1]) * inv4A;
+      rec.push_back({std::min(i, j), std::max(i, j), static_cast<int32_t>(k), G});
+    }
+  }
+  std::sort(rec.begin(), rec.end(), [](const Rec& x, const Rec& y) {
+    return x.lo != y.lo ? x.lo < y.lo : (x.hi != y.hi ? x.hi < y.hi : x.e < y.e);
+  });
+  m.edge_e0.clear();
+  m.edge_e1.clear();
+  m.edge_G0.clear();
+  m.edge_G1.clear();
+  std::vector<int32_t> elo, ehi;
+  for (size_t a = 0; a < rec.size();) {
+    size_t b = a + 1;
+    while (b < rec.size() && rec[b].lo == rec[a].lo && rec[b].hi == rec[a].hi) ++b;
+    if (b - a > 2) {
+      err = "mesh_add: an edge is shared by more than two triangles";
+      return kErrMesh;
+    }
+    const bool any_free = rec[a].lo < m.n_free || rec[a].hi < m.n_free;
+    const bool nonzero = rec[a].G != 0.0 || (b - a == 2 && rec[a + 1].G != 0.0);
+    if (any_free && nonzero) {
+      elo.push_back(rec[a].lo);
+      ehi.push_back(rec[a].hi);
+      m.edge_e0.push_back(rec[a].e);
+      m.edge_G0.push_back(rec[a].G);
+      m.edge_e1.push_back(b - a == 2 ? rec[a + 1].e : -1);
+      m.edge_G1.push_back(b - a == 2 ? rec[a + 1].G : 0.0);
+    }
+    a = b;
+  }
+  m.n_edges = static_cast<int64_t>(elo.size());
+  m.n_edges_P = 0;
+  for (int64_t k = 0; k < m.n_edges; ++k)
+    if (elo[k] < m.n_P) m.n_edges_P++;  // lo < hi, so a P endpoint means lo in P
+
+  // ---- adjacency of free nodes, sorted by neighbour -------------------------
+  std::vector<int32_t> count(m.n_free + 1, 0);
+  for (int64_t k = 0; k < m.n_edges; ++k) {
+    if (elo[k] < m.n_free) count[elo[k] + 1]++;
+    if (ehi[k] < m.n_free) count[ehi[k] + 1]++;
+  }
+  m.adj_ptr.assign(m.n_free + 1, 0);
+  for (int64_t k = 0; k < m.n_free; ++k) m.adj_ptr[k + 1] = m.adj_ptr[k] + count[k + 1];
+  m.adj_j.assign(m.adj_ptr[m.n_free], 0);
+  m.adj_e.assign(m.adj_ptr[m.n_free], 0);
+  std::vector<int32_t> fill(m.adj_ptr.begin(), m.adj_ptr.end() - 1);
+  for (int64_t k = 0; k < m.n_edges; ++k) {
+    if (elo[k] < m.n_free) {
+      m.adj_j[fill[elo[k]]] = ehi[k];
+      m.adj_e[fill[elo[k]]++] = static_cast<int32_t>(k);
+    }
+    if (ehi[k] < m.n_free) {
+      m.adj_j[fill[ehi[k]]] = elo[k];
+      m.adj_e[fill[ehi[k]]++] = static_cast<int32_t>(k);
+    }
+  }
+  for (int64_t i = 0; i < m.n_free; ++i) {
+    const int32_t a = m.adj_ptr[i], b = m.adj_ptr[i + 1];
+    std::vector<std::pair<int32_t, int32_t>> row;
+    for (int32_t t = a; t < b; ++t) row.emplace_back(m.adj_j[t], m.adj_e[t]);
+    std::sort(row.begin(), row.end());
+    for (int32_t t = a; t < b; ++t) {
+      m.adj_j[t] = row[t - a].first;
+      m.adj_e[t] = row[t - a].second;
     }
   }
   return 0;

@@ -6,13 +6,18 @@
 //   [ P nodes | R \ P nodes | free nodes outside R | Dirichlet nodes ]
 // where R = vertices of every element that has a vertex in P: the inner
 // substeps of Alg. 2 change exactly the nodes of R, all other free nodes
-// follow the closed-form leapfrog update.  Each free node lists its
-// incident elements with the two element-matrix entries that couple it to
-// the element's other vertices:
-//   (K u)_i = sum_{e ni i} c_e^2 ( G_e[i][j1] (u_j1 - u_i) + G_e[i][j2] (u_j2 - u_i) )
-// which uses that the rows of a P1 element matrix sum to zero.
-// G_e[a][b] = |T_e| grad(phi_a) . grad(phi_b) = (E_a . E_b) / (4 |T_e|), with
-// E_a the edge vector opposite vertex a taken in counter-clockwise order.
+// follow the closed-form leapfrog update.
+//
+// The stiffness is applied in edge form.  Rows of a P1 element matrix sum to
+// zero, so
+//   (K u)_i = sum_{j ~ i} K_ij (u_j - u_i),
+//   K_ij(w) = sum over the (one or two) elements e containing edge ij of
+//             c_e^2(w) G_e[i][j],
+//   G_e[a][b] = |T_e| grad(phi_a) . grad(phi_b) = (E_a . E_b) / (4 |T_e|),
+// with E_a the edge vector opposite vertex a in counter-clockwise order.
+// Edges whose element entries are all exactly zero (the hypotenuses of the
+// right triangles of a uniform grid) are dropped.  Each free node lists its
+// edges sorted by neighbour index, so the P neighbours come first.
 #pragma once
 #include <cstdint>
 #include <string>
@@ -25,9 +30,12 @@ struct HostMesh {
   int K = 0;   // field terms
   int KP = 0;  // K padded to 4, 8 or 16
   std::vector<int32_t> new2old, old2new;   // node permutation
-  std::vector<int32_t> inc_ptr;            // [n_free + 1]
-  std::vector<int32_t> inc_e, inc_j1, inc_j2;  // per incidence (new ids; element = new element id)
-  std::vector<double> inc_w1, inc_w2;      // G_e[i][j1], G_e[i][j2]
+  int64_t n_edges = 0;    // coupling edges kept (at least one free endpoint)
+  int64_t n_edges_P = 0;  // edges with a P endpoint (the inner substeps read these)
+  std::vector<int32_t> adj_ptr;            // [n_free + 1]
+  std::vector<int32_t> adj_j, adj_e;       // neighbour (new id) and edge id
+  std::vector<int32_t> edge_e0, edge_e1;   // element ids (new order), e1 = -1 on the boundary
+  std::vector<double> edge_G0, edge_G1;    // G_e0[i][j], G_e1[i][j] (0 when e1 = -1)
   std::vector<double> minv;                // [n_free] 1 / m_i (lumped mass)
   std::vector<double> psi2;                // [n_tri][KP] psi * log2(e), zero padded
 };

@@ -166,7 +166,7 @@ def lflts_mesh_add(ctx, xy, tri, dirichlet, P, psi):
 def lflts_mesh_info(ctx, mesh_id):
     info = np.zeros(8, dtype=np.int64)
     _check(ctx, load().lflts_mesh_info(ctx, mesh_id, _ptr(info)))
-    keys = ["n_nodes", "n_free", "n_R", "n_P", "n_tri", "K", "n_incidences", "KP"]
+    keys = ["n_nodes", "n_free", "n_R", "n_P", "n_tri", "K", "n_edges", "n_edges_P"]
     return {k: int(v) for k, v in zip(keys, info)}
 
 

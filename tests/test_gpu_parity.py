@@ -217,4 +217,4 @@ def test_profiling_counters(lf, ctx):
     assert co["launches"] == h.n_steps
     assert inn["launches"] == h.n_steps * 3
     assert co["ms"] > 0 and inn["alg_bytes"] > 0
-    assert lf.lflts_launch_count(ctx.h) - n0 == 2 + h.n_steps * 4 + 2
+    assert lf.lflts_launch_count(ctx.h) - n0 == 3 + h.n_steps * 4 + 2
