@@ -200,6 +200,36 @@ int lflts_run_pairs(lflts_ctx* ctx, const lflts_pair_job* jobs, int n_jobs,
                     int mem, void* stream);
 
 /*
+ * QoI reduction that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot let a library allocate device
+ * memory (their memory is owned by their own pool allocator, they must not
+ * allocate after start-up, or they are recording work into a CUDA graph,
+ * where cudaMalloc is not permitted).  It computes, like the QoI step of
+ * lflts_solve,
+ *     Q[s] = sum_k g[k] * u[idx[k]][s],   s = 0 .. S-1,
+ * in FP64 with compensated summation in the same order as lflts_solve.
+ *   ctx        optional (may be NULL); receives the error message
+ *   u          device [n_rows][S] state, FP32 (precision 32) or FP64 (64)
+ *   idx, g     device [nnz] row indices and FP64 weights; an index outside
+ *              [0, n_rows) is skipped (contributes nothing) and never read
+ *   Q          device [S] FP64 output
+ *   stream     cudaStream_t the two kernels are enqueued on
+ * Scratch: a fixed 2 MiB array in the library's device image, present on
+ * every GPU that loads the library until the process exits.  Its limit:
+ * ceil(nnz / 512) * S <= 131072 partial sums; larger calls return
+ * LFLTS_ERR_ARG without launching anything.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress, with the
+ * device current); make that first call before any stream capture.  All
+ * calls on a device share the array and every call overwrites what it
+ * reads, so nothing needs clearing, but calls whose kernels overlap on the
+ * GPU (different streams, no ordering between them) race on it.  The call
+ * makes no cudaMalloc/cudaFree and no allocating library call.
+ */
+int lflts_qoi_reduce_noalloc(lflts_ctx* ctx, const void* u, int precision, int64_t n_rows,
+                             int64_t S, const int32_t* idx, const double* g, int64_t nnz,
+                             double* Q, void* stream);
+
+/*
  * Profiling.  When enabled, every kernel launch is bracketed by CUDA events
  * on its stream; lflts_profile_read synchronises the context's device and
  * returns, per kernel class, the launch count, the summed device time in ms

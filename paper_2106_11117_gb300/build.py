@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblflts.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lflts.cu", "mesh_prep.cpp"]
+SOURCES = ["lflts.cu", "qoi_noalloc.cu", "mesh_prep.cpp"]
 DEPS = SOURCES + ["kernels.cuh", "mesh_prep.h"]
 
 

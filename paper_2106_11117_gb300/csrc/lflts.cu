@@ -469,6 +469,12 @@ int check_bad(lflts_ctx* c, cudaStream_t st) {
 
 }  // namespace
 
+// Error reporting for entry points defined in other translation units.
+int lflts_internal_set_error(lflts_ctx* ctx, int code, const char* msg) {
+  if (ctx) ctx->err = msg ? msg : "";
+  return code;
+}
+
 // ============================================================================
 // ABI
 // ============================================================================

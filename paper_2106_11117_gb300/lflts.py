@@ -36,6 +36,7 @@ EXPORTED = [
     "lflts_mesh_info", "lflts_mesh_order", "lflts_lts_constants", "lflts_field_add",
     "lflts_qoi_add", "lflts_solve", "lflts_level_sums", "lflts_run_pairs",
     "lflts_profile_enable", "lflts_profile_reset", "lflts_profile_read", "lflts_launch_count",
+    "lflts_qoi_reduce_noalloc",
 ]
 
 
@@ -95,6 +96,7 @@ def load(path: str | None = None):
         "lflts_profile_reset": (i32, [vp]),
         "lflts_profile_read": (i32, [vp, i32, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "lflts_launch_count": (i32, [vp, C.POINTER(i64)]),
+        "lflts_qoi_reduce_noalloc": (i32, [vp, vp, i32, i64, i64, vp, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -235,6 +237,12 @@ def lflts_launch_count(ctx):
     n = C.c_int64()
     _check(ctx, load().lflts_launch_count(ctx, C.byref(n)))
     return n.value
+
+
+def lflts_qoi_reduce_noalloc(ctx, u, precision, n_rows, S, idx, g, nnz, Q, stream=None):
+    """QoI reduction without allocation; all arrays are device buffers."""
+    return _check(ctx, load().lflts_qoi_reduce_noalloc(ctx, _ptr(u), int(precision), int(n_rows), int(S),
+                                                       _ptr(idx), _ptr(g), int(nnz), _ptr(Q), stream))
 
 
 # ------------------------------------------------------------ convenience
