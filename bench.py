@@ -324,6 +324,10 @@ def run_ours(args):
             "launches": pd["launches"], "avg_launch_ms": pd["ms"] / max(pd["launches"], 1),
             "share_of_kernel_time": round(pd["ms"] / sum(v["ms"] for v in prof.values()), 4)}
 
+    tte = None
+    if rank == 0 and not args.no_time_to_eps:
+        tte = time_to_eps(args.eps)
+
     cpu = None
     if pool is not None:
         cpu = cpu_baseline(args.config, pool.cores, pool=pool)
@@ -339,7 +343,7 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (per-mesh state >= 1 GB), no flush",
                            "parallelism": f"samples sharded, dp{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk,
+                "clocks": clk, "time_to_eps": tte,
                 "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                                        "alg_GBps": round(v["alg_bytes"] / (v["ms"] * 1e-3) / 1e9, 1)
                                        if v["ms"] > 0 else None} for k, v in prof.items()}}
@@ -347,6 +351,42 @@ def run_ours(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def time_to_eps(eps=2e-3):
+    """MLMC (Alg. 1) to RMSE eps on the plain workload square32-p4-K4
+    (3 levels used, a 4th available): batched FP32 path vs the per-draw FP64
+    path (one draw per launch), same draws, wall time of the whole Alg. 1."""
+    from paper_2106_11117_gb300 import lflts, mlmc
+    from workload import CONFIG_PLAIN, level_problem, xi_uniform
+    cfg = CONFIG_PLAIN
+    ctx = lflts.Context(0)
+    try:
+        hs = [ctx.add_level(level_problem(cfg, l)) for l in range(4)]
+
+        def w(h):
+            return h.n_steps * (h.info["n_free"] + h.p * h.info["n_R"])
+
+        def cost(l):
+            return float(w(hs[l]) + (w(hs[l - 1]) if l else 0))
+
+        def draw(l, off, n):
+            return xi_uniform(cfg.seed, l, n, cfg.K, offset=off)
+
+        def n_init(l):
+            return cfg.samples[l] if l < len(cfg.samples) else 16
+
+        out = {"eps": eps, "workload": cfg.name}
+        for name, plain in (("batched_fp32", False), ("plain_fp64", True)):
+            ev = mlmc.GpuLevelPairs(lflts, ctx, hs, precision=32, plain=plain)
+            r = mlmc.alg1(ev, draw, eps, cost, n_init, L_max=3)
+            out[name] = {"seconds": r.seconds, "estimate": r.estimate, "L": r.L, "N": r.N,
+                         "rmse_estimate": math.sqrt(r.mse), "calls": ev.calls}
+        out["speedup"] = out["plain_fp64"]["seconds"] / out["batched_fp32"]["seconds"]
+        out["estimate_diff"] = abs(out["plain_fp64"]["estimate"] - out["batched_fp32"]["estimate"])
+        return out
+    finally:
+        ctx.close()
 
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel
@@ -425,6 +465,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cores", type=int, default=0)
+    ap.add_argument("--no-time-to-eps", action="store_true")
+    ap.add_argument("--eps", type=float, default=2e-3)
     ap.add_argument("--profile-case", type=int, default=-1,
                     help="run only a few steps of one mesh solve (for ncu captures)")
     ap.add_argument("--profile-steps", type=int, default=4)

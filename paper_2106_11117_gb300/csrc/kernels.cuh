@@ -38,9 +38,24 @@ template <typename Real>
 struct MeshDev {
   int n_free, n_R, n_P;
   const int* __restrict__ adj_ptr;   // [n_free + 1]
-  const int2* __restrict__ adj;      // (neighbour, edge)
+  const int2* __restrict__ adj;      // (neighbour, edge), sorted by neighbour
+  const int4* __restrict__ ell;      // [n_free][2]: first four (neighbour, edge), neighbour -1 = empty
   const Real* __restrict__ minv;     // [n_free]
 };
+
+// The first four neighbours of node i (almost every node of the meshes has
+// exactly four stiffness neighbours): two 16-byte loads, no dependent chain.
+struct Nb4 {
+  int j[4], e[4];
+};
+template <typename Real>
+__device__ __forceinline__ Nb4 load_nb4(const MeshDev<Real>& m, int i) {
+  const int4 a = __ldg(m.ell + 2 * i), b = __ldg(m.ell + 2 * i + 1);
+  Nb4 r;
+  r.j[0] = a.x; r.e[0] = a.y; r.j[1] = a.z; r.e[1] = a.w;
+  r.j[2] = b.x; r.e[2] = b.y; r.j[3] = b.z; r.e[3] = b.w;
+  return r;
+}
 
 // --- vector access of VEC consecutive samples -------------------------------
 template <typename Real, int V>
@@ -145,24 +160,43 @@ k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real*
   if (s0 >= S) return;
   for (int i = blockIdx.x * l.NB + l.row; i < m.n_free; i += gridDim.x * l.NB) {
     const size_t is = (size_t)i * S + s0;
+    const bool outside = i >= m.n_R;
+    // issue every independent load of this node before any arithmetic
+    const Nb4 nb = load_nb4(m, i);
+    const int t0 = m.adj_ptr[i] + 4, t1 = m.adj_ptr[i + 1];
     const Pack<Real, VEC> ui = ldp<Real, VEC>(u + is);
+    Pack<Real, VEC> uj[4], w[4], dn;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (nb.j[q] >= 0) {
+        uj[q] = ldp<Real, VEC>(u + (size_t)nb.j[q] * S + s0);
+        w[q] = ldp<Real, VEC>(W + (size_t)nb.e[q] * S + s0);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) uj[q].v[k] = w[q].v[k] = Real(0);
+      }
+    }
+    if (outside) dn = ldp<Real, VEC>(d + is);
+    const Real mi = m.minv[i];
     Real acc[VEC];
 #pragma unroll
     for (int k = 0; k < VEC; ++k) acc[k] = Real(0);
-    const int t1 = m.adj_ptr[i + 1];
-    for (int t = m.adj_ptr[i]; t < t1; ++t) {
-      const int2 nb = m.adj[t];
-      const Pack<Real, VEC> uj = ldp<Real, VEC>(u + (size_t)nb.x * S + s0);
-      const Pack<Real, VEC> w = ldp<Real, VEC>(W + (size_t)nb.y * S + s0);
 #pragma unroll
-      for (int k = 0; k < VEC; ++k) acc[k] = fma(w.v[k], uj.v[k] - ui.v[k], acc[k]);
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) acc[k] = fma(w[q].v[k], uj[q].v[k] - ui.v[k], acc[k]);
+    for (int t = t0; t < t1; ++t) {  // neighbours beyond the fourth (rare)
+      const int2 o = m.adj[t];
+      const Pack<Real, VEC> uo = ldp<Real, VEC>(u + (size_t)o.x * S + s0);
+      const Pack<Real, VEC> wo = ldp<Real, VEC>(W + (size_t)o.y * S + s0);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) acc[k] = fma(wo.v[k], uo.v[k] - ui.v[k], acc[k]);
     }
-    const Real mi = m.minv[i];
     Pack<Real, VEC> gi;
 #pragma unroll
     for (int k = 0; k < VEC; ++k) gi.v[k] = mi * acc[k];
-    if (i >= m.n_R) {
-      Pack<Real, VEC> dn = ldp<Real, VEC>(d + is), un;
+    if (outside) {
+      Pack<Real, VEC> un;
 #pragma unroll
       for (int k = 0; k < VEC; ++k) {
         dn.v[k] = dn.v[k] - kappa_gamma * gi.v[k];
@@ -196,36 +230,60 @@ k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
   for (int i = blockIdx.x * l.NB + l.row; i < m.n_R; i += gridDim.x * l.NB) {
     const size_t is = (size_t)i * S + s0;
     const bool iP = i < nP;
+    // issue every independent load of this node before any arithmetic
+    const Nb4 nb = load_nb4(m, i);
+    const int t0 = m.adj_ptr[i] + 4, t1 = m.adj_ptr[i + 1];
     const Pack<Real, VEC> rc = ldp<Real, VEC>(cur + is);
+    const Pack<Real, VEC> gi = ldp<Real, VEC>(g + is);
+    Pack<Real, VEC> rj[4], w[4], rp;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = nb.j[q];
+      const bool jP = j >= 0 && j < nP;
+      // only P neighbours carry r; a P node also couples to its other neighbours
+      if (jP || (iP && j >= 0)) {
+        w[q] = ldp<Real, VEC>(W + (size_t)nb.e[q] * S + s0);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) w[q].v[k] = Real(0);
+      }
+      if (jP) {
+        rj[q] = ldp<Real, VEC>(cur + (size_t)j * S + s0);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) rj[q].v[k] = Real(0);
+      }
+    }
+    if (prev) {
+      rp = ldp<Real, VEC>(prev + is);
+    } else {
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) rp.v[k] = Real(0);
+    }
+    const Real mi = m.minv[i];
     Real vi[VEC], acc[VEC];
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
       vi[k] = iP ? s_cur * rc.v[k] : Real(0);
       acc[k] = Real(0);
     }
-    const int t1 = m.adj_ptr[i + 1];
-    for (int t = m.adj_ptr[i]; t < t1; ++t) {
-      const int2 nb = m.adj[t];
-      const bool jP = nb.x < nP;
-      if (!jP && !iP) break;  // neighbours sorted: no P neighbour left
-      const Pack<Real, VEC> w = ldp<Real, VEC>(W + (size_t)nb.y * S + s0);
-      if (jP) {
-        const Pack<Real, VEC> rj = ldp<Real, VEC>(cur + (size_t)nb.x * S + s0);
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] = fma(w.v[k], s_cur * rj.v[k] - vi[k], acc[k]);
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) acc[k] = fma(w[q].v[k], s_cur * rj[q].v[k] - vi[k], acc[k]);
+    for (int t = t0; t < t1; ++t) {  // neighbours beyond the fourth (rare)
+      const int2 o = m.adj[t];
+      const bool jP = o.x < nP;
+      if (!jP && !iP) break;  // sorted: no P neighbour left
+      const Pack<Real, VEC> wo = ldp<Real, VEC>(W + (size_t)o.y * S + s0);
+      if (jP) {
+        const Pack<Real, VEC> ro = ldp<Real, VEC>(cur + (size_t)o.x * S + s0);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) acc[k] = fma(wo.v[k], s_cur * ro.v[k] - vi[k], acc[k]);
       } else {
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] = fma(w.v[k], -vi[k], acc[k]);
+        for (int k = 0; k < VEC; ++k) acc[k] = fma(wo.v[k], -vi[k], acc[k]);
       }
-    }
-    const Real mi = m.minv[i];
-    const Pack<Real, VEC> gi = ldp<Real, VEC>(g + is);
-    Pack<Real, VEC> rp;
-    if (prev) {
-      rp = ldp<Real, VEC>(prev + is);
-    } else {
-#pragma unroll
-      for (int k = 0; k < VEC; ++k) rp.v[k] = Real(0);
     }
     Pack<Real, VEC> rn;
 #pragma unroll

@@ -36,6 +36,7 @@ struct MeshGPU {
   HostMesh h;
   int* adj_ptr = nullptr;
   int2* adj = nullptr;
+  int4* ell = nullptr;
   int2* ee = nullptr;       // elements of each edge
   float* eg32 = nullptr;    // [n_edges][2] element entries G
   double* eg64 = nullptr;
@@ -244,7 +245,7 @@ struct Sel;
 template <>
 struct Sel<float> {
   static MeshDev<float> mesh(const MeshGPU& m, int n_R) {
-    return MeshDev<float>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.adj_ptr, m.adj, m.minv32};
+    return MeshDev<float>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.adj_ptr, m.adj, m.ell, m.minv32};
   }
   static const float* field(const Field& f) { return f.v32; }
   static const float* eg(const MeshGPU& m) { return m.eg32; }
@@ -253,7 +254,7 @@ struct Sel<float> {
 template <>
 struct Sel<double> {
   static MeshDev<double> mesh(const MeshGPU& m, int n_R) {
-    return MeshDev<double>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.adj_ptr, m.adj, m.minv64};
+    return MeshDev<double>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.adj_ptr, m.adj, m.ell, m.minv64};
   }
   static const double* field(const Field& f) { return f.v64; }
   static const double* eg(const MeshGPU& m) { return m.eg64; }
@@ -551,6 +552,12 @@ int lflts_mesh_add(lflts_ctx* c, const double* xy, int64_t n_nodes, const int32_
     std::vector<float> psi32(h.psi2.begin(), h.psi2.end());
     LF_TRY(upload(c, &mg->adj_ptr, h.adj_ptr.data(), h.adj_ptr.size()));
     LF_TRY(upload(c, &mg->adj, adj.data(), na));
+    std::vector<int4> ell(static_cast<size_t>(h.n_free) * 2);
+    for (int64_t i = 0; i < h.n_free; ++i)
+      for (int hh = 0; hh < 2; ++hh)
+        ell[2 * i + hh] = make_int4(h.ell_j[4 * i + 2 * hh], h.ell_e[4 * i + 2 * hh], h.ell_j[4 * i + 2 * hh + 1],
+                                    h.ell_e[4 * i + 2 * hh + 1]);
+    LF_TRY(upload(c, &mg->ell, ell.data(), ell.size()));
     LF_TRY(upload(c, &mg->ee, ee.data(), ne));
     LF_TRY(upload(c, &mg->eg32, eg32.data(), eg32.size()));
     LF_TRY(upload(c, &mg->eg64, eg64.data(), eg64.size()));

@@ -183,14 +183,21 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
       m.adj_e[fill[ehi[k]]++] = static_cast<int32_t>(k);
     }
   }
+  std::vector<std::pair<int32_t, int32_t>> row;
+  m.ell_j.assign(static_cast<size_t>(m.n_free) * 4, -1);
+  m.ell_e.assign(static_cast<size_t>(m.n_free) * 4, 0);
   for (int64_t i = 0; i < m.n_free; ++i) {
     const int32_t a = m.adj_ptr[i], b = m.adj_ptr[i + 1];
-    std::vector<std::pair<int32_t, int32_t>> row;
+    row.clear();
     for (int32_t t = a; t < b; ++t) row.emplace_back(m.adj_j[t], m.adj_e[t]);
     std::sort(row.begin(), row.end());
     for (int32_t t = a; t < b; ++t) {
       m.adj_j[t] = row[t - a].first;
       m.adj_e[t] = row[t - a].second;
+      if (t - a < 4) {
+        m.ell_j[4 * i + (t - a)] = row[t - a].first;
+        m.ell_e[4 * i + (t - a)] = row[t - a].second;
+      }
     }
   }
   return 0;

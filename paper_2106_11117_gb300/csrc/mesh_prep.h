@@ -34,6 +34,10 @@ struct HostMesh {
   int64_t n_edges_P = 0;  // edges with a P endpoint (the inner substeps read these)
   std::vector<int32_t> adj_ptr;            // [n_free + 1]
   std::vector<int32_t> adj_j, adj_e;       // neighbour (new id) and edge id
+  // The first four entries of every adjacency list again in a fixed-width
+  // table [n_free][4] (neighbour, edge), padded with neighbour -1; entries
+  // beyond the fourth stay in adj_j/adj_e from adj_ptr[i] + 4 on.
+  std::vector<int32_t> ell_j, ell_e;
   std::vector<int32_t> edge_e0, edge_e1;   // element ids (new order), e1 = -1 on the boundary
   std::vector<double> edge_G0, edge_G1;    // G_e0[i][j], G_e1[i][j] (0 when e1 = -1)
   std::vector<double> minv;                // [n_free] 1 / m_i (lumped mass)
