@@ -200,6 +200,26 @@ int lflts_run_pairs(lflts_ctx* ctx, const lflts_pair_job* jobs, int n_jobs,
                     int mem, void* stream);
 
 /*
+ * Gradient of the QoI with respect to the field parameters: for every draw
+ * s, Q[s] (as lflts_solve) and dQdxi[s][k] = dQ/dxi_k, the exact derivative of
+ * the computed (discrete) QoI.  Discrete adjoint of the u-form LF-LTS solve:
+ * the adjoint variable obeys the same step operator backwards (the LF-LTS
+ * step is self-adjoint in the M inner product, the basis of the energy
+ * identity of Alg. 2), the inner substeps are differentiated by their own
+ * adjoint recursion near P, and the derivative of c_e^2 = exp(xi . psi_e) is
+ * psi_{e,k} c_e^2.  States are stored every `ckpt_every` outer steps and
+ * recomputed forward within a segment, because running leapfrog backwards
+ * in floating point drifts.  The paper has no adjoint: it is an extension
+ * for gradient-based use (sensitivities, inversion) of the same solve.
+ *   xi     [S][K] FP64 draws;  Q [S] FP64;  dQdxi [S][K] FP64, row-major
+ *   memory: about (2 ceil(N/ckpt_every) + ckpt_every + 6) state arrays of
+ *           n_nodes x S values plus 2p arrays on R and n_edges x S FP64
+ * Errors as lflts_solve; LFLTS_ERR_ARG for ckpt_every < 1.
+ */
+int lflts_grad_xi(lflts_ctx* ctx, const lflts_solve_desc* desc, const double* xi, int64_t S,
+                  int ckpt_every, double* Q, double* dQdxi, int mem, void* stream);
+
+/*
  * QoI reduction that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot let a library allocate device
  * memory (their memory is owned by their own pool allocator, they must not

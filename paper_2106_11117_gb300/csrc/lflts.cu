@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/lflts.h"
+#include "adjoint.cuh"
 #include "kernels.cuh"
 #include "mesh_prep.h"
 
@@ -38,6 +39,7 @@ struct MeshGPU {
   int2* adj = nullptr;
   int4* ell = nullptr;
   int2* ee = nullptr;       // elements of each edge
+  int2* ends = nullptr;     // endpoints of each edge (i < j)
   float* eg32 = nullptr;    // [n_edges][2] element entries G
   double* eg64 = nullptr;
   float* minv32 = nullptr;
@@ -64,6 +66,11 @@ struct Workspace {
   Buf ua, ub, d, g, r0, r1, r2, W, xipad, xraw, qps, qpc, Q, uN;
 };
 
+// Buffers of the adjoint (gradient) solve.
+struct GradBufs {
+  Buf ckpt, segU, rs, rho, gs, A, nua, nub, dnu, part, xraw, Q, G;
+};
+
 struct ProfRec {
   int cls;
   cudaEvent_t a, b;
@@ -80,6 +87,8 @@ struct lflts_ctx {
   std::vector<Field> fields;
   std::vector<Qoi> qois;
   std::vector<std::unique_ptr<Workspace>> ws;
+  std::unique_ptr<Workspace> gws;   // forward buffers of lflts_grad_xi
+  std::unique_ptr<GradBufs> gb;     // adjoint buffers of lflts_grad_xi
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> sync_events;
   int* d_bad = nullptr;
@@ -266,34 +275,40 @@ Geo geometry_vec(const lflts_ctx* c, int64_t n, int64_t S, int vec) {
   return geometry(c, n, S / vec);
 }
 
-// The time loop of Alg. 2 for one batch (see kernels.cuh for the u-form).
+// One step of Alg. 2 for one batch (see kernels.cuh for the u-form): the
+// coarse launch over the free nodes, then p-1 inner launches over R.
 template <typename Real, int VEC>
-int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S,
-              Workspace& ws, Real*& uc_out, cudaStream_t st) {
-  const HostMesh& h = mg.h;
-  const size_t rb = sizeof(Real);
-  const int p = ds.p;
-  Real* ua = static_cast<Real*>(ws.ua.p);
-  Real* ub = static_cast<Real*>(ws.ub.p);
-  Real* d = static_cast<Real*>(ws.d.p);
-  Real* g = static_cast<Real*>(ws.g.p);
-  Real* rbuf[3] = {static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p)};
-  const Real* W = static_cast<const Real*>(ws.W.p);
-
+struct Stepper {
+  lflts_ctx* c = nullptr;
+  MeshDev<Real> md{};
+  Geo gc{}, gi{};
   std::vector<double> beta, cm;
-  double delta, omega, c0, gamma;
-  lts_constants(p, ds.nu, ds.dt, beta, cm, delta, omega, c0, gamma);
-  const MeshDev<Real> md = Sel<Real>::mesh(mg, n_R);
-  const Geo gc = geometry_vec(c, h.n_free, S, VEC);
-  const Geo gi = geometry_vec(c, std::max(n_R, 1), S, VEC);
-  const double Srb = double(S) * rb;
-  const double coarse_bytes = Srb * (4.0 * h.n_free - 2.0 * n_R + double(h.n_edges));
-  const double edgeP_bytes = Srb * double(h.n_edges_P);
+  double delta = 0, omega = 0, c0 = 0, gamma = 0;
+  int p = 1, n_R = 0;
+  int64_t S = 0;
+  double Srb = 0, coarse_bytes = 0, edgeP_bytes = 0;
+  const Real* W = nullptr;
+  Real* g = nullptr;
+  Real* rbuf[3] = {nullptr, nullptr, nullptr};
 
-  Real* uc = ua;
-  Real* un = ub;
-  for (int64_t n = 0; n < ds.n_steps; ++n) {
-    const Real kappa = (n == 0) ? Real(1) : Real(2);
+  Stepper(lflts_ctx* c_, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R_, int64_t S_, const Real* W_,
+          Real* g_, Real* r0, Real* r1, Real* r2)
+      : c(c_), p(ds.p), n_R(n_R_), S(S_), W(W_), g(g_) {
+    const HostMesh& h = mg.h;
+    rbuf[0] = r0;
+    rbuf[1] = r1;
+    rbuf[2] = r2;
+    lts_constants(p, ds.nu, ds.dt, beta, cm, delta, omega, c0, gamma);
+    md = Sel<Real>::mesh(mg, n_R);
+    gc = geometry_vec(c, h.n_free, S, VEC);
+    gi = geometry_vec(c, std::max(n_R, 1), S, VEC);
+    Srb = double(S) * sizeof(Real);
+    coarse_bytes = Srb * (4.0 * h.n_free - 2.0 * n_R + double(h.n_edges));
+    edgeP_bytes = Srb * double(h.n_edges_P);
+  }
+
+  // u_next = 2 T u_cur - u_prev in increments: d += kappa r_p, u_next = u_cur + d.
+  int step(const Real* uc, Real* un, Real* d, Real kappa, cudaStream_t st) {
     {
       Prof pr(c, st);
       k_coarse<Real, VEC><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g,
@@ -331,6 +346,21 @@ int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n
         nxt = (nxt + 1) % 3;
       }
     }
+    return 0;
+  }
+};
+
+// The time loop of Alg. 2 for one batch.
+template <typename Real, int VEC>
+int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S,
+              Workspace& ws, Real*& uc_out, cudaStream_t st) {
+  Stepper<Real, VEC> stp(c, ds, mg, n_R, S, static_cast<const Real*>(ws.W.p), static_cast<Real*>(ws.g.p),
+                         static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p));
+  Real* uc = static_cast<Real*>(ws.ua.p);
+  Real* un = static_cast<Real*>(ws.ub.p);
+  Real* d = static_cast<Real*>(ws.d.p);
+  for (int64_t n = 0; n < ds.n_steps; ++n) {
+    LF_TRY(stp.step(uc, un, d, (n == 0) ? Real(1) : Real(2), st));
     std::swap(uc, un);
   }
   uc_out = uc;
@@ -468,6 +498,224 @@ int check_bad(lflts_ctx* c, cudaStream_t st) {
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Gradient of the QoI with respect to xi: discrete adjoint (adjoint.cuh),
+// checkpoints every k outer steps, forward recomputation inside a segment.
+// ---------------------------------------------------------------------------
+template <typename Real, int VEC, int KP>
+int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64_t S, int k_ck, double* d_Q,
+             double* d_G, cudaStream_t st) {
+  const MeshGPU& mg = *c->meshes[ds.mesh_id];
+  const HostMesh& h = mg.h;
+  const Qoi& q = c->qois[ds.qoi_id];
+  const Field& u0 = c->fields[ds.u0_field];
+  const Field* v0 = ds.v0_field >= 0 ? &c->fields[ds.v0_field] : nullptr;
+  if (!c->gws) c->gws.reset(new Workspace());
+  if (!c->gb) c->gb.reset(new GradBufs());
+  Workspace& ws = *c->gws;
+  GradBufs& gb = *c->gb;
+  const int p = ds.p;
+  const int n_R = p > 1 ? static_cast<int>(h.n_R) : 0;
+  const int nP_eff = p > 1 ? static_cast<int>(h.n_P) : 0;
+  const int64_t N = ds.n_steps;
+  const int64_t n_nodes = h.n_nodes;
+  const size_t rb = sizeof(Real);
+  const size_t state = size_t(n_nodes) * S * rb, rsz = size_t(std::max(n_R, 1)) * S * rb;
+  const int64_t k = std::max<int64_t>(1, std::min<int64_t>(k_ck, N));
+  const int64_t n_ck = (N + k - 1) / k;
+  LF_TRY(ensure(c, ws.ua, state));
+  LF_TRY(ensure(c, ws.ub, state));
+  LF_TRY(ensure(c, ws.d, state));
+  LF_TRY(ensure(c, ws.g, rsz));
+  LF_TRY(ensure(c, ws.r0, rsz));
+  LF_TRY(ensure(c, ws.r1, rsz));
+  LF_TRY(ensure(c, ws.r2, rsz));
+  LF_TRY(ensure(c, ws.W, size_t(std::max<int64_t>(h.n_edges, 1)) * S * rb));
+  LF_TRY(ensure(c, ws.xipad, size_t(S) * KP * rb));
+  LF_TRY(ensure(c, gb.ckpt, size_t(n_ck) * 2 * state));
+  LF_TRY(ensure(c, gb.segU, size_t(k) * state));
+  LF_TRY(ensure(c, gb.rs, size_t(std::max(p - 2, 1)) * rsz));
+  LF_TRY(ensure(c, gb.rho, size_t(std::max(p - 1, 1)) * rsz));
+  LF_TRY(ensure(c, gb.gs, rsz));
+  LF_TRY(ensure(c, gb.A, size_t(std::max<int64_t>(h.n_edges, 1)) * S * sizeof(double)));
+  LF_TRY(ensure(c, gb.nua, state));
+  LF_TRY(ensure(c, gb.nub, state));
+  LF_TRY(ensure(c, gb.dnu, state));
+  Real* ua = static_cast<Real*>(ws.ua.p);
+  Real* ub = static_cast<Real*>(ws.ub.p);
+  Real* d = static_cast<Real*>(ws.d.p);
+  Real* xi = static_cast<Real*>(ws.xipad.p);
+  Real* W = static_cast<Real*>(ws.W.p);
+  Real* ckpt = static_cast<Real*>(gb.ckpt.p);
+  Real* segU = static_cast<Real*>(gb.segU.p);
+  Real* rs = static_cast<Real*>(gb.rs.p);
+  Real* rho = static_cast<Real*>(gb.rho.p);
+  Real* gs = static_cast<Real*>(gb.gs.p);
+  double* A = static_cast<double*>(gb.A.p);
+  const size_t sn = size_t(n_nodes) * S;  // elements per state array
+  const size_t rn = size_t(std::max(n_R, 1)) * S;
+
+  {  // a1 and start values, as in lflts_solve
+    Prof pr(c, st);
+    k_xi_pad<Real, KP><<<blocks_for(S * KP, 256, 4096), 256, 0, st>>>((int)S, h.K, d_xi, xi);
+    LF_CUDA(c, cudaGetLastError());
+    k_init_state<Real><<<blocks_for(n_nodes * S, 256, c->sms * 32), 256, 0, st>>>(
+        n_nodes, (int)S, Sel<Real>::field(u0), v0 ? Sel<Real>::field(*v0) : nullptr, (Real)ds.dt, ua, ub, d);
+    LF_CUDA(c, cudaGetLastError());
+    const Geo ge = geometry(c, std::max<int64_t>(h.n_edges, 1), S);
+    k_edge_weights<Real, KP><<<ge.grid, 256, 0, st>>>(h.n_edges, (int)S, ge.SB, mg.ee, Sel<Real>::eg(mg),
+                                                      Sel<Real>::psi(mg), xi, W);
+    LF_CUDA(c, cudaGetLastError());
+    pr.end(LFLTS_KERNEL_INIT, double(S) * rb * (3.0 * n_nodes + double(h.n_edges)));
+    c->launches += 2;
+  }
+  Stepper<Real, VEC> stp(c, ds, mg, n_R, S, W, static_cast<Real*>(ws.g.p), static_cast<Real*>(ws.r0.p),
+                         static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p));
+
+  // ---- forward with checkpoints of (u_n, d_n) every k steps --------------
+  Real* uc = ua;
+  Real* un = ub;
+  for (int64_t n = 0; n < N; ++n) {
+    if (n % k == 0) {
+      LF_CUDA(c, cudaMemcpyAsync(ckpt + (2 * (n / k)) * sn, uc, state, cudaMemcpyDeviceToDevice, st));
+      LF_CUDA(c, cudaMemcpyAsync(ckpt + (2 * (n / k) + 1) * sn, d, state, cudaMemcpyDeviceToDevice, st));
+    }
+    LF_TRY(stp.step(uc, un, d, (n == 0) ? Real(1) : Real(2), st));
+    std::swap(uc, un);
+  }
+  {  // QoI of u_N
+    const int chunk = 512;
+    const int n_chunks = std::max(1, (q.nnz + chunk - 1) / chunk);
+    LF_TRY(ensure(c, ws.qps, size_t(n_chunks) * S * sizeof(double)));
+    LF_TRY(ensure(c, ws.qpc, size_t(n_chunks) * S * sizeof(double)));
+    const int tb = static_cast<int>(std::min<int64_t>(S, 128));
+    Prof pr(c, st);
+    k_qoi_partial<Real><<<dim3(n_chunks, static_cast<unsigned>((S + tb - 1) / tb)), tb, 0, st>>>(
+        uc, (int)S, q.idx, q.g, q.nnz, chunk, static_cast<double*>(ws.qps.p), static_cast<double*>(ws.qpc.p));
+    LF_CUDA(c, cudaGetLastError());
+    k_qoi_final<<<blocks_for(S, 128, 1 << 20), 128, 0, st>>>(n_chunks, (int)S, static_cast<double*>(ws.qps.p),
+                                                            static_cast<double*>(ws.qpc.p), d_Q, c->d_bad);
+    LF_CUDA(c, cudaGetLastError());
+    pr.end(LFLTS_KERNEL_QOI, double(q.nnz) * S * rb);
+    c->launches++;
+  }
+
+  // ---- adjoint seed nu_N = M^-1 g_Q, d nu = nu_N, A = 0 --------------------
+  Real* vc = static_cast<Real*>(gb.nua.p);
+  Real* vn = static_cast<Real*>(gb.nub.p);
+  Real* dv = static_cast<Real*>(gb.dnu.p);
+  LF_CUDA(c, cudaMemsetAsync(vc, 0, state, st));
+  LF_CUDA(c, cudaMemsetAsync(vn, 0, state, st));
+  LF_CUDA(c, cudaMemsetAsync(dv, 0, state, st));
+  LF_CUDA(c, cudaMemsetAsync(A, 0, size_t(std::max<int64_t>(h.n_edges, 1)) * S * sizeof(double), st));
+  // the step kernels write free nodes only: Dirichlet rows of the recomputed
+  // states must hold 0 (the edge accumulation reads them)
+  LF_CUDA(c, cudaMemsetAsync(segU, 0, size_t(k) * state, st));
+  k_adj_seed<Real><<<blocks_for(int64_t(q.nnz) * S, 256, c->sms * 16), 256, 0, st>>>(
+      q.nnz, (int)S, q.idx, q.g, mg.minv64, (int)h.n_free, vc, dv);
+  LF_CUDA(c, cudaGetLastError());
+  c->launches++;
+
+  MeshDev<Real> mdR = Sel<Real>::mesh(mg, n_R);
+  mdR.n_free = n_R;  // g = a(u) on R only
+  const Geo gR = geometry_vec(c, std::max(n_R, 1), S, VEC);
+  const Geo gE = geometry(c, std::max<int64_t>(h.n_edges, 1), S);
+  AdjConsts kc{};
+  kc.p = p;
+  kc.gamma = stp.gamma;
+  kc.c[0] = stp.c0;
+  for (int m = 1; m < p; ++m) kc.c[m] = stp.cm[m];
+
+  // ---- segments, last to first ------------------------------------------------
+  for (int64_t seg = n_ck - 1; seg >= 0; --seg) {
+    const int64_t n0 = seg * k, n1 = std::min(N, n0 + k);
+    LF_CUDA(c, cudaMemcpyAsync(segU, ckpt + (2 * seg) * sn, state, cudaMemcpyDeviceToDevice, st));
+    LF_CUDA(c, cudaMemcpyAsync(d, ckpt + (2 * seg + 1) * sn, state, cudaMemcpyDeviceToDevice, st));
+    for (int64_t n = n0; n + 1 < n1; ++n)
+      LF_TRY(stp.step(segU + (n - n0) * sn, segU + (n - n0 + 1) * sn, d, (n == 0) ? Real(1) : Real(2), st));
+    for (int64_t n = n1 - 1; n >= n0; --n) {
+      const Real kappa = (n == 0) ? Real(1) : Real(2);
+      const Real* u_n = segU + (n - n0) * sn;
+      if (n_R > 0) {
+        // (i) g = a(u_n) on R; (ii) r_2 .. r_{p-1} of the inner recursion
+        k_coarse<Real, VEC><<<gR.grid, 256, 0, st>>>(mdR, (int)S, gR.SB, W, u_n, nullptr, nullptr, gs, Real(0));
+        LF_CUDA(c, cudaGetLastError());
+        c->launches++;
+        for (int m = 1; m <= p - 2; ++m) {
+          const Real* cur = (m == 1) ? gs : rs + (m - 2) * rn;
+          const Real s_cur = (m == 1) ? (Real)(-stp.c0) : Real(1);
+          const Real* prv = (m == 1) ? nullptr : ((m == 2) ? gs : rs + (m - 3) * rn);
+          const Real s_prv = (m == 2) ? (Real)(-stp.c0) : Real(1);
+          k_inner<Real, VEC, false><<<gR.grid, 256, 0, st>>>(
+              stp.md, (int)S, gR.SB, W, cur, s_cur, prv, s_prv, rs + (m - 1) * rn, gs, nullptr, nullptr, nullptr,
+              (Real)(1.0 + stp.beta[m]), (Real)stp.beta[m], (Real)stp.cm[m], Real(0));
+          LF_CUDA(c, cudaGetLastError());
+          c->launches++;
+        }
+        // (iii) inner adjoint rho_{p-1} .. rho_1 (rho_p = kappa nu_{n+1})
+        for (int m = p - 1; m >= 1; --m) {
+          const Real* s1p = (m + 1 == p) ? vc : rho + m * rn;
+          const Real s1 = (m + 1 == p) ? kappa : Real(1);
+          const Real* s2p = (m + 2 == p) ? vc : ((m + 2 < p) ? rho + (m + 1) * rn : nullptr);
+          const Real s2 = (m + 2 == p) ? kappa : Real(1);
+          const Real b1 = (m + 1 <= p - 1) ? (Real)stp.beta[m + 1] : Real(0);
+          k_adj_inner<Real, VEC><<<gR.grid, 256, 0, st>>>(stp.md, (int)S, gR.SB, W, s1p, s1, s2p, s2,
+                                                           rho + (m - 1) * rn, (Real)(1.0 + stp.beta[m]), b1,
+                                                           (Real)stp.cm[m]);
+          LF_CUDA(c, cudaGetLastError());
+          c->launches++;
+        }
+      }
+      // (iv) edge accumulators
+      kc.kappa = double(kappa);
+      k_adj_edges<Real><<<gE.grid, 256, 0, st>>>(h.n_edges, nP_eff, n_R, (int)S, gE.SB, mg.ends, u_n, vc, gs, rs,
+                                                 rho, A, kc);
+      LF_CUDA(c, cudaGetLastError());
+      c->launches++;
+      // (v) nu_n = 2 T nu_{n+1} - nu_{n+2}
+      if (n > 0) {
+        LF_TRY(stp.step(vc, vn, dv, Real(2), st));
+        std::swap(vc, vn);
+      }
+    }
+  }
+
+  // ---- dQ/dxi_k = sum_edges A_e dK_e/dxi_k ------------------------------------
+  const int64_t chunk = 4096;
+  const int64_t n_chunks = std::max<int64_t>(1, (h.n_edges + chunk - 1) / chunk);
+  LF_TRY(ensure(c, gb.part, size_t(n_chunks) * S * h.K * sizeof(double)));
+  const int tb = static_cast<int>(std::min<int64_t>(S, 128));
+  k_grad_contract<KP><<<dim3(static_cast<unsigned>(n_chunks), static_cast<unsigned>((S + tb - 1) / tb)), tb, 0, st>>>(
+      h.n_edges, (int)S, chunk, mg.ee, mg.eg64, mg.psi64, d_xi, h.K, A, static_cast<double*>(gb.part.p));
+  LF_CUDA(c, cudaGetLastError());
+  k_grad_finish<<<blocks_for(S * h.K, 128, 1 << 20), 128, 0, st>>>((int)n_chunks, (int)S, h.K,
+                                                                   static_cast<double*>(gb.part.p), d_G);
+  LF_CUDA(c, cudaGetLastError());
+  c->launches += 2;
+  return 0;
+}
+
+template <typename Real, int VEC>
+int run_grad_kp(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64_t S, int k_ck, double* d_Q,
+                double* d_G, cudaStream_t st) {
+  switch (c->meshes[ds.mesh_id]->h.KP) {
+    case 4: return run_grad<Real, VEC, 4>(c, ds, d_xi, S, k_ck, d_Q, d_G, st);
+    case 8: return run_grad<Real, VEC, 8>(c, ds, d_xi, S, k_ck, d_Q, d_G, st);
+    default: return run_grad<Real, VEC, 16>(c, ds, d_xi, S, k_ck, d_Q, d_G, st);
+  }
+}
+
+int grad_device(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64_t S, int k_ck, double* d_Q,
+                double* d_G, cudaStream_t st) {
+  if (ds.precision == 32) {
+    if (S % 4 == 0) return run_grad_kp<float, 4>(c, ds, d_xi, S, k_ck, d_Q, d_G, st);
+    if (S % 2 == 0) return run_grad_kp<float, 2>(c, ds, d_xi, S, k_ck, d_Q, d_G, st);
+    return run_grad_kp<float, 1>(c, ds, d_xi, S, k_ck, d_Q, d_G, st);
+  }
+  if (S % 2 == 0) return run_grad_kp<double, 2>(c, ds, d_xi, S, k_ck, d_Q, d_G, st);
+  return run_grad_kp<double, 1>(c, ds, d_xi, S, k_ck, d_Q, d_G, st);
+}
+
 }  // namespace
 
 // Error reporting for entry points defined in other translation units.
@@ -510,6 +758,15 @@ int lflts_destroy(lflts_ctx* c) {
     for (auto& w : c->ws)
       for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->W, &w->xipad, &w->xraw, &w->qps,
                      &w->qpc, &w->Q, &w->uN})
+        if (b->p) cudaFree(b->p);
+    for (Workspace* w : {c->gws.get()})
+      if (w)
+        for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->W, &w->xipad, &w->xraw, &w->qps,
+                       &w->qpc, &w->Q, &w->uN})
+          if (b->p) cudaFree(b->p);
+    if (c->gb)
+      for (Buf* b : {&c->gb->ckpt, &c->gb->segU, &c->gb->rs, &c->gb->rho, &c->gb->gs, &c->gb->A, &c->gb->nua,
+                     &c->gb->nub, &c->gb->dnu, &c->gb->part, &c->gb->xraw, &c->gb->Q, &c->gb->G})
         if (b->p) cudaFree(b->p);
     for (void* p : c->owned) cudaFree(p);
     for (auto s : c->streams) cudaStreamDestroy(s);
@@ -559,6 +816,9 @@ int lflts_mesh_add(lflts_ctx* c, const double* xy, int64_t n_nodes, const int32_
                                     h.ell_e[4 * i + 2 * hh + 1]);
     LF_TRY(upload(c, &mg->ell, ell.data(), ell.size()));
     LF_TRY(upload(c, &mg->ee, ee.data(), ne));
+    std::vector<int2> ends(ne);
+    for (size_t k = 0; k < ne; ++k) ends[k] = make_int2(h.edge_i[k], h.edge_j[k]);
+    LF_TRY(upload(c, &mg->ends, ends.data(), ne));
     LF_TRY(upload(c, &mg->eg32, eg32.data(), eg32.size()));
     LF_TRY(upload(c, &mg->eg64, eg64.data(), eg64.size()));
     LF_TRY(upload(c, &mg->minv32, minv32.data(), minv32.size()));
@@ -834,6 +1094,33 @@ int lflts_run_pairs(lflts_ctx* c, const lflts_pair_job* jobs, int n_jobs, int me
   }
   if (mem == LFLTS_MEM_HOST) return check_bad(c, st);
   return LFLTS_OK;
+}
+
+int lflts_grad_xi(lflts_ctx* c, const lflts_solve_desc* ds, const double* xi, int64_t S, int ckpt_every,
+                  double* Q, double* dQdxi, int mem, void* stream) {
+  if (!c) return LFLTS_ERR_ARG;
+  c->err.clear();
+  LF_TRY(set_device(c));
+  LF_TRY(check_desc(c, ds));
+  if (S < 1 || S > kMaxS) return fail(c, LFLTS_ERR_ARG, "grad_xi: S must be in [1, 2097120]");
+  if (!xi || !Q || !dQdxi) return fail(c, LFLTS_ERR_ARG, "grad_xi: null xi, Q or dQdxi");
+  if (ckpt_every < 1) return fail(c, LFLTS_ERR_ARG, "grad_xi: ckpt_every must be >= 1");
+  if (mem != LFLTS_MEM_HOST && mem != LFLTS_MEM_DEVICE) return fail(c, LFLTS_ERR_ARG, "grad_xi: bad mem kind");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const HostMesh& h = c->meshes[ds->mesh_id]->h;
+  LF_TRY(reset_bad(c, st));
+  if (mem == LFLTS_MEM_DEVICE) return grad_device(c, *ds, xi, S, ckpt_every, Q, dQdxi, st);
+  if (!c->gb) c->gb.reset(new GradBufs());
+  GradBufs& gb = *c->gb;
+  LF_TRY(ensure(c, gb.xraw, size_t(S) * h.K * sizeof(double)));
+  LF_TRY(ensure(c, gb.Q, size_t(S) * sizeof(double)));
+  LF_TRY(ensure(c, gb.G, size_t(S) * h.K * sizeof(double)));
+  LF_CUDA(c, cudaMemcpyAsync(gb.xraw.p, xi, size_t(S) * h.K * sizeof(double), cudaMemcpyHostToDevice, st));
+  LF_TRY(grad_device(c, *ds, static_cast<double*>(gb.xraw.p), S, ckpt_every, static_cast<double*>(gb.Q.p),
+                     static_cast<double*>(gb.G.p), st));
+  LF_CUDA(c, cudaMemcpyAsync(Q, gb.Q.p, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  LF_CUDA(c, cudaMemcpyAsync(dQdxi, gb.G.p, size_t(S) * h.K * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return check_bad(c, st);
 }
 
 int lflts_profile_enable(lflts_ctx* c, int on) {

@@ -158,6 +158,8 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
     a = b;
   }
   m.n_edges = static_cast<int64_t>(elo.size());
+  m.edge_i = elo;
+  m.edge_j = ehi;
   m.n_edges_P = 0;
   for (int64_t k = 0; k < m.n_edges; ++k)
     if (elo[k] < m.n_P) m.n_edges_P++;  // lo < hi, so a P endpoint means lo in P

@@ -36,7 +36,7 @@ EXPORTED = [
     "lflts_mesh_info", "lflts_mesh_order", "lflts_lts_constants", "lflts_field_add",
     "lflts_qoi_add", "lflts_solve", "lflts_level_sums", "lflts_run_pairs",
     "lflts_profile_enable", "lflts_profile_reset", "lflts_profile_read", "lflts_launch_count",
-    "lflts_qoi_reduce_noalloc",
+    "lflts_qoi_reduce_noalloc", "lflts_grad_xi",
 ]
 
 
@@ -97,6 +97,7 @@ def load(path: str | None = None):
         "lflts_profile_read": (i32, [vp, i32, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "lflts_launch_count": (i32, [vp, C.POINTER(i64)]),
         "lflts_qoi_reduce_noalloc": (i32, [vp, vp, i32, i64, i64, vp, vp, i64, vp, vp]),
+        "lflts_grad_xi": (i32, [vp, C.POINTER(SolveDesc), vp, i64, i32, vp, vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -209,6 +210,11 @@ def lflts_solve(ctx, desc: SolveDesc, xi, S, Q, uN=None, mem=LFLTS_MEM_HOST, str
                                           int(mem), stream))
 
 
+def lflts_grad_xi(ctx, desc: SolveDesc, xi, S, ckpt_every, Q, dQdxi, mem=LFLTS_MEM_HOST, stream=None):
+    return _check(ctx, load().lflts_grad_xi(ctx, C.byref(desc), _ptr(xi), int(S), int(ckpt_every), _ptr(Q),
+                                            _ptr(dQdxi), int(mem), stream))
+
+
 def lflts_level_sums(ctx, Qf, Qc, S, sums, mem=LFLTS_MEM_HOST, stream=None):
     return _check(ctx, load().lflts_level_sums(ctx, _ptr(Qf), _ptr(Qc), int(S), _ptr(sums), int(mem), stream))
 
@@ -289,6 +295,14 @@ class Context:
         fid = lflts_field_add(self.h, mid, level["u0"])
         return LevelHandle(mid, qid, fid, level["dt"], level["n_steps"], level["p"], level["nu"],
                            lflts_mesh_info(self.h, mid))
+
+    def grad(self, lv: LevelHandle, xi, precision=64, ckpt_every=16):
+        """Host convenience: xi [S, K] -> (Q [S], dQ/dxi [S, K])."""
+        xi = np.ascontiguousarray(xi, dtype=np.float64)
+        S, K = xi.shape
+        Q, G = np.zeros(S), np.zeros((S, K))
+        lflts_grad_xi(self.h, lv.desc(precision), xi, S, ckpt_every, Q, G, LFLTS_MEM_HOST, None)
+        return Q, G
 
     def solve(self, lv: LevelHandle, xi, precision=32, state=False, p=None):
         """Host convenience: xi [S, K] numpy -> Q [S] (and u_N [n_nodes, S])."""
