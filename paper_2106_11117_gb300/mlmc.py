@@ -111,6 +111,43 @@ class GpuLevelPairs:
         return out
 
 
+class ShardedLevelPairs:
+    """Splits every level's draws across ranks (contiguous blocks, no data
+    exchange) and combines the per-level sums of all ranks.
+
+    Draws are independent (the MLMC sample is an independent sample,
+    Sec. 2.2), so rank r evaluates rows [n r / world, n (r+1) / world) of each
+    request with its own evaluator.  The only exchange is the level sums:
+    every rank all-gathers the per-rank 4-vectors and adds them with
+    compensated summation in rank order, so all ranks take identical Alg. 1
+    decisions.  ``gather(vec) -> list of vecs`` is the collective (e.g.
+    torch.distributed.all_gather_object); dQ stays local."""
+
+    def __init__(self, evaluator, rank, world, gather):
+        self.ev = evaluator
+        self.rank = rank
+        self.world = world
+        self.gather = gather
+        self.calls = 0
+
+    def run(self, requests):
+        local = {}
+        for l, xi in requests.items():
+            n = xi.shape[0]
+            lo, hi = n * self.rank // self.world, n * (self.rank + 1) // self.world
+            local[l] = xi[lo:hi]
+        nonempty = {l: x for l, x in local.items() if x.shape[0] > 0}
+        res = self.ev.run(nonempty) if nonempty else {}
+        self.calls += 1
+        mine = {l: (list(res[l][1]) if l in res else [0.0, 0.0, 0.0, 0.0]) for l in requests}
+        allv = self.gather(mine)
+        out = {}
+        for l in requests:
+            sums = [_csum(v[l][k] for v in allv) for k in range(4)]
+            out[l] = (res[l][0] if l in res else np.zeros(0), sums)
+        return out
+
+
 # ------------------------------------------------------------ Alg. 1
 @dataclass
 class MLMCResult:
