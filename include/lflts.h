@@ -66,6 +66,14 @@ enum {
   LFLTS_KERNEL_CLASSES = 5
 };
 
+/* Options for lflts_set_option. */
+enum {
+  LFLTS_OPT_GRAPHS = 1,   /* 1 (default): solves on a non-default stream are captured once into a
+                             CUDA graph and replayed while problem, batch and buffers are unchanged */
+  LFLTS_OPT_AUTOTUNE = 2  /* 1 (default): the first solve of a (mesh, S, precision, p) times the
+                             candidate launch shapes (draws per thread, CTAs per SM) and keeps the best */
+};
+
 /* Library version (major*10000 + minor*100 + patch). */
 int lflts_version(void);
 
@@ -264,6 +272,16 @@ int lflts_profile_reset(lflts_ctx* ctx);
 int lflts_profile_read(lflts_ctx* ctx, int kernel_class, int64_t* launches,
                        double* ms, double* alg_bytes);
 int lflts_launch_count(lflts_ctx* ctx, int64_t* launches);
+
+/* Set an LFLTS_OPT_* option of the context. */
+int lflts_set_option(lflts_ctx* ctx, int option, int64_t value);
+
+/*
+ * Counters: out[0] kernel launches executed (kernels inside replayed graphs
+ * counted one by one), out[1] graph launches, out[2] kernel launches spent
+ * in autotuning (not in out[0]), out[3] autotuned launch shapes cached.
+ */
+int lflts_get_stats(lflts_ctx* ctx, int64_t out[4]);
 
 #ifdef __cplusplus
 }

@@ -151,8 +151,8 @@ k_edge_weights(int64_t n_edges, int S, int SB, const int2* __restrict__ ee,
 //   outside R: d += -kappa*gamma*g, u_next = u_n + d
 //   inside  R: store g
 // ---------------------------------------------------------------------------
-template <typename Real, int VEC>
-__global__ void __launch_bounds__(256)
+template <typename Real, int VEC, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB)
 k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real* __restrict__ u,
          Real* __restrict__ u_next, Real* __restrict__ d, Real* __restrict__ g, Real kappa_gamma) {
   const Lane l = lane_of(SB);
@@ -216,8 +216,8 @@ k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real*
 // r_m = s_cur * cur, r_{m-1} = s_prev * prev (prev == nullptr: r_0 = 0).
 // LAST: fold r_p into d and u_next instead of storing it.
 // ---------------------------------------------------------------------------
-template <typename Real, int VEC, bool LAST>
-__global__ void __launch_bounds__(256)
+template <typename Real, int VEC, bool LAST, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB)
 k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
         const Real* __restrict__ cur, Real s_cur, const Real* __restrict__ prev, Real s_prev,
         Real* __restrict__ r_next, const Real* __restrict__ g, const Real* __restrict__ u,

@@ -47,6 +47,8 @@ struct MeshGPU {
   float* psi32 = nullptr;
   double* psi64 = nullptr;
   int* new2old = nullptr;
+  // autotuned (vec, CTAs per SM) per (S, precision, p)
+  std::map<std::tuple<int64_t, int, int>, std::pair<int, int>> tuned;
 };
 
 struct Field {
@@ -62,8 +64,25 @@ struct Qoi {
   double* g = nullptr;
 };
 
+// Everything a captured solve graph depends on.
+struct GraphKey {
+  int mesh, qoi, u0, v0, precision, p;
+  double nu, dt;
+  int64_t n_steps, S;
+  const void *xi, *Q, *uN, *ua, *ub, *d, *g, *r0, *r1, *r2, *W, *xipad, *qps, *qpc;
+  int vec, cps;
+  bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+  int64_t kernels;
+};
+
 struct Workspace {
   Buf ua, ub, d, g, r0, r1, r2, W, xipad, xraw, qps, qpc, Q, uN;
+  std::vector<GraphEntry> graphs;
 };
 
 // Buffers of the adjoint (gradient) solve.
@@ -100,6 +119,10 @@ struct lflts_ctx {
   double prof_ms[LFLTS_KERNEL_CLASSES] = {0};
   double prof_bytes[LFLTS_KERNEL_CLASSES] = {0};
   int64_t launches = 0;
+  int64_t tune_launches = 0;
+  int64_t graph_launches = 0;
+  bool graphs = true;
+  bool autotune = true;
   std::vector<void*> owned;  // device allocations of meshes, fields, QoIs
 };
 
@@ -225,7 +248,7 @@ struct Geo {
 // (grid-stride), grid y the sample slabs; about 16 CTAs of 256 threads per SM.
 // SB is the largest lane count that leaves at most a quarter of the lanes of
 // the sample slabs idle.
-Geo geometry(const lflts_ctx* c, int64_t n, int64_t SV) {
+Geo geometry(const lflts_ctx* c, int64_t n, int64_t SV, int cta_per_sm = 16) {
   int SB = 1;
   for (int sb = 32; sb > 1; sb /= 2) {
     const int64_t waste = ((SV + sb - 1) / sb) * sb - SV;
@@ -236,7 +259,7 @@ Geo geometry(const lflts_ctx* c, int64_t n, int64_t SV) {
   }
   const int NB = 256 / SB;
   const int64_t gy = (SV + SB - 1) / SB;
-  const int64_t target = int64_t(c->sms) * 16;
+  const int64_t target = int64_t(c->sms) * cta_per_sm;
   int64_t gx = std::max<int64_t>(1, std::min<int64_t>((n + NB - 1) / NB, std::max<int64_t>(1, target / gy)));
   Geo g;
   g.grid = dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy), 1);
@@ -271,8 +294,8 @@ struct Sel<double> {
 };
 
 // Geometry of the node/edge kernels: SB lanes of VEC samples per node.
-Geo geometry_vec(const lflts_ctx* c, int64_t n, int64_t S, int vec) {
-  return geometry(c, n, S / vec);
+Geo geometry_vec(const lflts_ctx* c, int64_t n, int64_t S, int vec, int cta_per_sm = 16) {
+  return geometry(c, n, S / vec, cta_per_sm);
 }
 
 // One step of Alg. 2 for one batch (see kernels.cuh for the u-form): the
@@ -290,29 +313,37 @@ struct Stepper {
   const Real* W = nullptr;
   Real* g = nullptr;
   Real* rbuf[3] = {nullptr, nullptr, nullptr};
+  bool minb6 = false;
 
   Stepper(lflts_ctx* c_, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R_, int64_t S_, const Real* W_,
-          Real* g_, Real* r0, Real* r1, Real* r2)
+          Real* g_, Real* r0, Real* r1, Real* r2, int shape = 16)
       : c(c_), p(ds.p), n_R(n_R_), S(S_), W(W_), g(g_) {
+    // shape = CTAs per SM target, +100 for the register-capped kernels
+    minb6 = shape >= 100;
+    const int cta_per_sm = shape % 100;
     const HostMesh& h = mg.h;
     rbuf[0] = r0;
     rbuf[1] = r1;
     rbuf[2] = r2;
     lts_constants(p, ds.nu, ds.dt, beta, cm, delta, omega, c0, gamma);
     md = Sel<Real>::mesh(mg, n_R);
-    gc = geometry_vec(c, h.n_free, S, VEC);
-    gi = geometry_vec(c, std::max(n_R, 1), S, VEC);
+    gc = geometry_vec(c, h.n_free, S, VEC, cta_per_sm);
+    gi = geometry_vec(c, std::max(n_R, 1), S, VEC, cta_per_sm);
     Srb = double(S) * sizeof(Real);
     coarse_bytes = Srb * (4.0 * h.n_free - 2.0 * n_R + double(h.n_edges));
     edgeP_bytes = Srb * double(h.n_edges_P);
   }
 
   // u_next = 2 T u_cur - u_prev in increments: d += kappa r_p, u_next = u_cur + d.
+  // minb6: the register-capped instantiation (at least 6 CTAs of 256 per SM).
   int step(const Real* uc, Real* un, Real* d, Real kappa, cudaStream_t st) {
     {
       Prof pr(c, st);
-      k_coarse<Real, VEC><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g,
-                                                    (Real)(double(kappa) * gamma));
+      const Real kg = (Real)(double(kappa) * gamma);
+      if (minb6)
+        k_coarse<Real, VEC, 6><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg);
+      else
+        k_coarse<Real, VEC, 1><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg);
       LF_CUDA(c, cudaGetLastError());
       pr.end(LFLTS_KERNEL_COARSE, coarse_bytes);
     }
@@ -328,12 +359,17 @@ struct Stepper {
         const Real opb = (Real)(1.0 + beta[m]), bt = (Real)beta[m], cmm = (Real)cm[m];
         Real* rn = rbuf[nxt];
         Prof pr(c, st);
-        if (last)
-          k_inner<Real, VEC, true><<<gi.grid, 256, 0, st>>>(md, (int)S, gi.SB, W, cur, s_cur, prev, s_prev, rn, g,
-                                                            uc, un, d, opb, bt, cmm, kappa);
-        else
-          k_inner<Real, VEC, false><<<gi.grid, 256, 0, st>>>(md, (int)S, gi.SB, W, cur, s_cur, prev, s_prev, rn, g,
-                                                             uc, un, d, opb, bt, cmm, kappa);
+#define LF_INNER(L, B)                                                                                    \
+  k_inner<Real, VEC, L, B><<<gi.grid, 256, 0, st>>>(md, (int)S, gi.SB, W, cur, s_cur, prev, s_prev, rn, g, \
+                                                    uc, un, d, opb, bt, cmm, kappa)
+        if (last) {
+          if (minb6) LF_INNER(true, 6);
+          else LF_INNER(true, 1);
+        } else {
+          if (minb6) LF_INNER(false, 6);
+          else LF_INNER(false, 1);
+        }
+#undef LF_INNER
         LF_CUDA(c, cudaGetLastError());
         // values per R node: cur, prev (unless it is g), g, the new r (or d, u in, d, u out)
         const double reads = (m == 1 ? 1.0 : (m == 2 ? 2.0 : 3.0));
@@ -353,13 +389,15 @@ struct Stepper {
 // The time loop of Alg. 2 for one batch.
 template <typename Real, int VEC>
 int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S,
-              Workspace& ws, Real*& uc_out, cudaStream_t st) {
+              Workspace& ws, Real*& uc_out, cudaStream_t st, int cta_per_sm = 16, int64_t n_steps = -1) {
   Stepper<Real, VEC> stp(c, ds, mg, n_R, S, static_cast<const Real*>(ws.W.p), static_cast<Real*>(ws.g.p),
-                         static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p));
+                         static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p),
+                         cta_per_sm);
   Real* uc = static_cast<Real*>(ws.ua.p);
   Real* un = static_cast<Real*>(ws.ub.p);
   Real* d = static_cast<Real*>(ws.d.p);
-  for (int64_t n = 0; n < ds.n_steps; ++n) {
+  const int64_t N = n_steps >= 0 ? n_steps : ds.n_steps;
+  for (int64_t n = 0; n < N; ++n) {
     LF_TRY(stp.step(uc, un, d, (n == 0) ? Real(1) : Real(2), st));
     std::swap(uc, un);
   }
@@ -367,8 +405,79 @@ int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n
   return 0;
 }
 
+template <typename Real>
+int time_loop_vec(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
+                  Real*& uc, cudaStream_t st, int vec, int cps, int64_t n_steps = -1) {
+  if (vec == 4) return time_loop<Real, 4>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps);
+  if (vec == 2) return time_loop<Real, 2>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps);
+  return time_loop<Real, 1>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps);
+}
+
+// Launch shape of the step kernels for a batch: draws per thread (vec),
+// CTAs per SM and the register cap (shape code cps: CTAs per SM, +100 for the
+// instantiation limited to 40 registers so that 6 CTAs of 256 fit an SM).  With autotuning on, the first solve of a (mesh, S,
+// precision, p) times every candidate over a few steps on the real buffers
+// (the state is re-initialised afterwards) and keeps the fastest.
+template <typename Real>
+int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
+                 cudaStream_t st, int& vec, int& cps) {
+  const int vmax = (sizeof(Real) == 4) ? 4 : 2;
+  std::vector<int> vecs;
+  for (int v = vmax; v >= 1; v /= 2)
+    if (S % v == 0) vecs.push_back(v);
+  vec = vecs.front();
+  cps = 16;
+  if (!c->autotune) return 0;
+  const auto key = std::make_tuple(S, ds.precision, ds.p);
+  auto it = mg.tuned.find(key);
+  if (it != mg.tuned.end()) {
+    vec = it->second.first;
+    cps = it->second.second;
+    return 0;
+  }
+  cudaEvent_t e0, e1;
+  LF_CUDA(c, cudaEventCreate(&e0));
+  LF_CUDA(c, cudaEventCreate(&e1));
+  const bool prof = c->profiling;
+  c->profiling = false;
+  const int64_t launches0 = c->launches;
+  float best = 1e30f;
+  const int64_t steps = std::min<int64_t>(4, ds.n_steps);
+  for (int v : vecs) {
+    if (vecs.size() > 2 && v == 1) continue;
+    for (int k : {8, 16, 32, 108, 116, 132}) {
+      Real* uc = nullptr;
+      int rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, 1);  // warm
+      if (!rc) rc = cudaEventRecord(e0, st) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
+      if (!rc) rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, steps);
+      if (!rc) rc = cudaEventRecord(e1, st) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
+      if (!rc) rc = cudaEventSynchronize(e1) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
+      float ms = 0.f;
+      if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+      if (rc) {
+        c->profiling = prof;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+      }
+      if (ms < best) {
+        best = ms;
+        vec = v;
+        cps = k;
+      }
+    }
+  }
+  c->tune_launches += c->launches - launches0;
+  c->launches = launches0;  // tuning launches are reported separately
+  c->profiling = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  mg.tuned[key] = std::make_pair(vec, cps);
+  return 0;
+}
+
 template <typename Real, int KP>
-int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, const Qoi& q,
+int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qoi& q,
                  const Field& u0, const Field* v0, const double* d_xi, int64_t S, double* d_Q,
                  double* d_uN, Workspace& ws, cudaStream_t st) {
   const HostMesh& h = mg.h;
@@ -378,6 +487,9 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, co
   const int n_R = (p > 1) ? static_cast<int>(h.n_R) : 0;
   const size_t state_bytes = size_t(n_nodes) * S * rb;
   const size_t r_bytes = size_t(std::max(n_R, 1)) * S * rb;
+  const int chunk = 512;
+  const int n_chunks = std::max(1, (q.nnz + chunk - 1) / chunk);
+  // every buffer is sized before the first launch (no allocation during graph capture)
   LF_TRY(ensure(c, ws.ua, state_bytes));
   LF_TRY(ensure(c, ws.ub, state_bytes));
   LF_TRY(ensure(c, ws.d, state_bytes));
@@ -387,13 +499,15 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, co
   LF_TRY(ensure(c, ws.r2, r_bytes));
   LF_TRY(ensure(c, ws.W, size_t(std::max<int64_t>(h.n_edges, 1)) * S * rb));
   LF_TRY(ensure(c, ws.xipad, size_t(S) * KP * rb));
+  LF_TRY(ensure(c, ws.qps, size_t(n_chunks) * S * sizeof(double)));
+  LF_TRY(ensure(c, ws.qpc, size_t(n_chunks) * S * sizeof(double)));
   Real* ua = static_cast<Real*>(ws.ua.p);
   Real* ub = static_cast<Real*>(ws.ub.p);
   Real* d = static_cast<Real*>(ws.d.p);
   Real* xi = static_cast<Real*>(ws.xipad.p);
   Real* W = static_cast<Real*>(ws.W.p);
 
-  {  // a1: draws, initial state, per-sample edge weights of K(w)
+  auto a1 = [&]() -> int {  // a1: draws, initial state, per-sample edge weights of K(w)
     Prof pr(c, st);
     k_xi_pad<Real, KP><<<blocks_for(S * KP, 256, 4096), 256, 0, st>>>((int)S, h.K, d_xi, xi);
     LF_CUDA(c, cudaGetLastError());
@@ -406,46 +520,115 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, co
     LF_CUDA(c, cudaGetLastError());
     pr.end(LFLTS_KERNEL_INIT, double(S) * rb * (3.0 * n_nodes + double(h.n_edges)));
     c->launches += 2;  // three kernels in this class
+    return 0;
+  };
+
+  int vec = 1, cps = 16;
+  if (c->autotune && !mg.tuned.count(std::make_tuple(S, ds.precision, ds.p))) {
+    const int64_t l0 = c->launches;
+    const bool prof = c->profiling;
+    c->profiling = false;
+    const int rc = a1();  // edge weights and a valid state for the timing runs
+    c->profiling = prof;
+    LF_TRY(rc);
+    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps));
+    c->tune_launches += c->launches - l0;
+    c->launches = l0;
+  } else {
+    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps));
   }
 
-  Real* uc = nullptr;
-  const int vmax = (sizeof(Real) == 4) ? 4 : 2;
-  int vec = 1;
-  if (S % vmax == 0) vec = vmax;
-  else if (S % 2 == 0) vec = 2;
-  if (vec == 4) LF_TRY((time_loop<Real, 4>(c, ds, mg, n_R, S, ws, uc, st)));
-  else if (vec == 2) LF_TRY((time_loop<Real, 2>(c, ds, mg, n_R, S, ws, uc, st)));
-  else LF_TRY((time_loop<Real, 1>(c, ds, mg, n_R, S, ws, uc, st)));
+  auto body = [&]() -> int {
+    LF_TRY(a1());
+    Real* uc = nullptr;
+    LF_TRY(time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, vec, cps));
+    {  // QoI at t_N (Sec. 2.1), FP64 compensated accumulation.
+      const int tb = static_cast<int>(std::min<int64_t>(S, 128));
+      Prof pr(c, st);
+      k_qoi_partial<Real><<<dim3(n_chunks, static_cast<unsigned>((S + tb - 1) / tb)), tb, 0, st>>>(
+          uc, (int)S, q.idx, q.g, q.nnz, chunk, static_cast<double*>(ws.qps.p), static_cast<double*>(ws.qpc.p));
+      LF_CUDA(c, cudaGetLastError());
+      k_qoi_final<<<blocks_for(S, 128, 1 << 20), 128, 0, st>>>(n_chunks, (int)S, static_cast<double*>(ws.qps.p),
+                                                              static_cast<double*>(ws.qpc.p), d_Q, c->d_bad);
+      LF_CUDA(c, cudaGetLastError());
+      pr.end(LFLTS_KERNEL_QOI, double(q.nnz) * S * rb);
+      c->launches++;
+    }
+    if (d_uN) {
+      k_gather_state<Real><<<blocks_for(n_nodes * S, 256, c->sms * 32), 256, 0, st>>>(n_nodes, (int)S, mg.new2old,
+                                                                                     uc, d_uN);
+      LF_CUDA(c, cudaGetLastError());
+      c->launches++;
+    }
+    return 0;
+  };
 
-  // QoI at t_N (Sec. 2.1), FP64 compensated accumulation.
-  {
-    const int chunk = 512;
-    const int n_chunks = std::max(1, (q.nnz + chunk - 1) / chunk);
-    LF_TRY(ensure(c, ws.qps, size_t(n_chunks) * S * sizeof(double)));
-    LF_TRY(ensure(c, ws.qpc, size_t(n_chunks) * S * sizeof(double)));
-    const int tb = static_cast<int>(std::min<int64_t>(S, 128));
-    Prof pr(c, st);
-    k_qoi_partial<Real><<<dim3(n_chunks, static_cast<unsigned>((S + tb - 1) / tb)), tb, 0, st>>>(
-        uc, (int)S, q.idx, q.g, q.nnz, chunk, static_cast<double*>(ws.qps.p), static_cast<double*>(ws.qpc.p));
-    LF_CUDA(c, cudaGetLastError());
-    k_qoi_final<<<blocks_for(S, 128, 1 << 20), 128, 0, st>>>(n_chunks, (int)S, static_cast<double*>(ws.qps.p),
-                                                            static_cast<double*>(ws.qpc.p), d_Q, c->d_bad);
-    LF_CUDA(c, cudaGetLastError());
-    pr.end(LFLTS_KERNEL_QOI, double(q.nnz) * S * rb);
-    c->launches++;
+  // CUDA graph of the whole solve (one launch instead of ~p N), replayed while
+  // the problem, the batch and the buffers stay the same.
+  const bool use_graph = c->graphs && !c->profiling && st != nullptr;
+  if (!use_graph) return body();
+  GraphKey key;
+  std::memset(&key, 0, sizeof(key));  // padding too: keys compare bytewise
+  key.mesh = ds.mesh_id;
+  key.qoi = ds.qoi_id;
+  key.u0 = ds.u0_field;
+  key.v0 = ds.v0_field;
+  key.precision = ds.precision;
+  key.p = ds.p;
+  key.nu = ds.nu;
+  key.dt = ds.dt;
+  key.n_steps = ds.n_steps;
+  key.S = S;
+  key.xi = d_xi;
+  key.Q = d_Q;
+  key.uN = d_uN;
+  key.ua = ws.ua.p;
+  key.ub = ws.ub.p;
+  key.d = ws.d.p;
+  key.g = ws.g.p;
+  key.r0 = ws.r0.p;
+  key.r1 = ws.r1.p;
+  key.r2 = ws.r2.p;
+  key.W = ws.W.p;
+  key.xipad = ws.xipad.p;
+  key.qps = ws.qps.p;
+  key.qpc = ws.qpc.p;
+  key.vec = vec;
+  key.cps = cps;
+  for (auto& ge : ws.graphs)
+    if (ge.key == key) {
+      LF_CUDA(c, cudaGraphLaunch(ge.exec, st));
+      c->launches += ge.kernels;
+      c->graph_launches++;
+      return 0;
+    }
+  const int64_t l0 = c->launches;
+  LF_CUDA(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const int rc = body();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
   }
-  if (d_uN) {
-    k_gather_state<Real><<<blocks_for(n_nodes * S, 256, c->sms * 32), 256, 0, st>>>(n_nodes, (int)S, mg.new2old, uc, d_uN);
-    LF_CUDA(c, cudaGetLastError());
-    c->launches++;
-  }
+  if (ec != cudaSuccess) return fail(c, LFLTS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+  const int64_t kernels = c->launches - l0;
+  c->launches = l0;
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return fail(c, LFLTS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+  ws.graphs.push_back({key, exec, kernels});
+  LF_CUDA(c, cudaGraphLaunch(exec, st));
+  c->launches += kernels;
+  c->graph_launches++;
   return 0;
 }
 
 template <typename Real>
 int run_solve(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64_t S, double* d_Q,
               double* d_uN, Workspace& ws, cudaStream_t st) {
-  const MeshGPU& mg = *c->meshes[ds.mesh_id];
+  MeshGPU& mg = *c->meshes[ds.mesh_id];
   const Qoi& q = c->qois[ds.qoi_id];
   const Field& u0 = c->fields[ds.u0_field];
   const Field* v0 = ds.v0_field >= 0 ? &c->fields[ds.v0_field] : nullptr;
@@ -755,6 +938,8 @@ int lflts_destroy(lflts_ctx* c) {
   if (c->device >= 0) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    for (auto& w : c->ws)
+      for (auto& ge : w->graphs) cudaGraphExecDestroy(ge.exec);
     for (auto& w : c->ws)
       for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->W, &w->xipad, &w->xraw, &w->qps,
                      &w->qpc, &w->Q, &w->uN})
@@ -1164,6 +1349,25 @@ int lflts_profile_read(lflts_ctx* c, int cls, int64_t* launches, double* ms, dou
   if (launches) *launches = c->prof_launches[cls];
   if (ms) *ms = c->prof_ms[cls];
   if (bytes) *bytes = c->prof_bytes[cls];
+  return LFLTS_OK;
+}
+
+int lflts_set_option(lflts_ctx* c, int option, int64_t value) {
+  if (!c) return LFLTS_ERR_ARG;
+  switch (option) {
+    case LFLTS_OPT_GRAPHS: c->graphs = value != 0; return LFLTS_OK;
+    case LFLTS_OPT_AUTOTUNE: c->autotune = value != 0; return LFLTS_OK;
+    default: return fail(c, LFLTS_ERR_ARG, "set_option: unknown option");
+  }
+}
+
+int lflts_get_stats(lflts_ctx* c, int64_t out[4]) {
+  if (!c || !out) return LFLTS_ERR_ARG;
+  out[0] = c->launches;
+  out[1] = c->graph_launches;
+  out[2] = c->tune_launches;
+  out[3] = 0;
+  for (auto& m : c->meshes) out[3] += static_cast<int64_t>(m->tuned.size());
   return LFLTS_OK;
 }
 

@@ -36,8 +36,10 @@ EXPORTED = [
     "lflts_mesh_info", "lflts_mesh_order", "lflts_lts_constants", "lflts_field_add",
     "lflts_qoi_add", "lflts_solve", "lflts_level_sums", "lflts_run_pairs",
     "lflts_profile_enable", "lflts_profile_reset", "lflts_profile_read", "lflts_launch_count",
-    "lflts_qoi_reduce_noalloc", "lflts_grad_xi",
+    "lflts_qoi_reduce_noalloc", "lflts_grad_xi", "lflts_set_option", "lflts_get_stats",
 ]
+LFLTS_OPT_GRAPHS = 1
+LFLTS_OPT_AUTOTUNE = 2
 
 
 class LibraryNotBuilt(RuntimeError):
@@ -98,6 +100,8 @@ def load(path: str | None = None):
         "lflts_launch_count": (i32, [vp, C.POINTER(i64)]),
         "lflts_qoi_reduce_noalloc": (i32, [vp, vp, i32, i64, i64, vp, vp, i64, vp, vp]),
         "lflts_grad_xi": (i32, [vp, C.POINTER(SolveDesc), vp, i64, i32, vp, vp, i32, vp]),
+        "lflts_set_option": (i32, [vp, i32, i64]),
+        "lflts_get_stats": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -237,6 +241,17 @@ def lflts_profile_read(ctx, kernel_class):
     n, ms, b = C.c_int64(), C.c_double(), C.c_double()
     _check(ctx, load().lflts_profile_read(ctx, cls, C.byref(n), C.byref(ms), C.byref(b)))
     return {"launches": n.value, "ms": ms.value, "alg_bytes": b.value}
+
+
+def lflts_set_option(ctx, option, value):
+    return _check(ctx, load().lflts_set_option(ctx, int(option), int(value)))
+
+
+def lflts_get_stats(ctx):
+    out = np.zeros(4, dtype=np.int64)
+    _check(ctx, load().lflts_get_stats(ctx, _ptr(out)))
+    return {"launches": int(out[0]), "graph_launches": int(out[1]), "tune_launches": int(out[2]),
+            "tuned_shapes": int(out[3])}
 
 
 def lflts_launch_count(ctx):

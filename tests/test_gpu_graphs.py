@@ -1,0 +1,79 @@
+"""CUDA-graph replay and autotuned launch shapes change nothing in the
+results (needs a GB300)."""
+import numpy as np
+import pytest
+
+from gpu_common import draws, small_level
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_11117_gb300 import build, lflts
+    build.build()
+    return lflts
+
+
+def _jobs(lf, hs, xis, outs, prec):
+    jobs = []
+    for l in range(len(hs)):
+        j = lf.PairJob()
+        j.fine = hs[l].desc(prec)
+        if l > 0:
+            j.coarse = hs[l - 1].desc(prec)
+            j.has_coarse = 1
+        j.xi = xis[l].ctypes.data
+        j.S = xis[l].shape[0]
+        j.dQ, j.Qf, j.sums = (o.ctypes.data for o in outs[l])
+        jobs.append(j)
+    return jobs
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_graph_replay_and_autotune_bit_identical(lf, prec):
+    levs = [small_level(n=8 * 2**l, p=2 + l, K=4, box=(0.375, 0.625, 0.375, 0.625)) for l in range(3)]
+    xis = [draws(S, 4, seed=60 + S) for S in (64, 20, 9)]
+    results = {}
+    for graphs, tune in ((0, 0), (1, 0), (1, 1), (0, 1)):
+        ctx = lf.Context(0)
+        try:
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_GRAPHS, graphs)
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_AUTOTUNE, tune)
+            hs = [ctx.add_level(l) for l in levs]
+            runs = []
+            for _ in range(3):  # first call captures, the next ones replay
+                outs = [(np.zeros(x.shape[0]), np.zeros(x.shape[0]), np.zeros(4)) for x in xis]
+                lf.lflts_run_pairs(ctx.h, _jobs(lf, hs, xis, outs, prec))
+                runs.append(outs)
+            st = lf.lflts_get_stats(ctx.h)
+            if graphs:
+                assert st["graph_launches"] >= 3 * 3
+            else:
+                assert st["graph_launches"] == 0
+            if tune:
+                assert st["tuned_shapes"] >= 3 and st["tune_launches"] > 0
+        finally:
+            ctx.close()
+        for r in runs[1:]:
+            for a, b in zip(r, runs[0]):
+                for x, y in zip(a, b):
+                    np.testing.assert_array_equal(x, y)
+        results[(graphs, tune)] = runs[0]
+    ref = results[(0, 0)]
+    for key, r in results.items():
+        for a, b in zip(r, ref):
+            for x, y in zip(a, b):
+                np.testing.assert_array_equal(x, y)
+
+
+def test_unknown_option_rejected(lf):
+    ctx = lf.Context(0)
+    try:
+        with pytest.raises(lf.LfltsError):
+            lf.lflts_set_option(ctx.h, 99, 1)
+    finally:
+        ctx.close()
