@@ -319,7 +319,8 @@ def run_ours(args):
     achieved = pd["alg_bytes"] / (pd["ms"] * 1e-3) / 1e9 if pd["ms"] > 0 else 0.0
     roof = {"bound": "hbm", "kernel": {"coarse": "k_coarse", "inner": "k_inner"}[dom],
             "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+            "frac": round(achieved / peak, 4),
+            "traffic": (TRAFFIC_RATIO[dom] * pd["alg_bytes"] / max(pd["launches"], 1)) if dom in TRAFFIC_RATIO else None,
             "alg_bytes_per_launch": pd["alg_bytes"] / max(pd["launches"], 1),
             "launches": pd["launches"], "avg_launch_ms": pd["ms"] / max(pd["launches"], 1),
             "share_of_kernel_time": round(pd["ms"] / sum(v["ms"] for v in prof.values()), 4)}
@@ -389,10 +390,11 @@ def time_to_eps(eps=2e-3):
         ctx.close()
 
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel
-# class, scaled to one launch of this workload (None until captured for the
-# current kernels).
-TRAFFIC_PER_LAUNCH = {}
+# DRAM traffic per launch = algorithmic bytes x (dram__bytes_read.sum +
+# dram__bytes_write.sum) / algorithmic bytes of one ncu capture of the same
+# kernel on a smaller batch (traffic grows in proportion to the draws):
+# profiles/k_inner_square128-L3-S32.md (k_inner unchanged since the capture).
+TRAFFIC_RATIO = {"inner": 657.9 / 619.0}
 
 
 def run_reference(args):
@@ -428,6 +430,73 @@ def run_reference(args):
                              "sample": f"{cores} level-0 solves per step, {args.steps} timed steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_lts_vs_lf(args):
+    """LF-LTS vs standard leapfrog (global step dt/p, the same mesh without P)
+    on the first levels of the batched workload: measured solve times against
+    the cost model (Eqs. cost_waveeq_LF / cost_waveeq_LTS) and the MLMC
+    speed-up S of Prop. 3.2 with the variances of the batch."""
+    import numpy as np
+    import torch
+    from paper_2106_11117_gb300 import build, costmodel, lflts
+    from workload import level_problem, xi_uniform
+    build.build()
+    cfg = _cfg(args.config)
+    levels = list(range(min(args.lts_vs_lf_levels, cfg.levels)))
+    ctx = lflts.Context(0)
+    st = torch.cuda.Stream()
+    out = {"mode": "lts_vs_lf", "workload": cfg.name, "levels": []}
+    Q = {}
+    for l in levels:
+        lev = level_problem(cfg, l)
+        h_lts = ctx.add_level(lev)
+        lev_lf = dict(lev, dt=lev["dt"] / cfg.p, n_steps=lev["n_steps"] * cfg.p)
+        h_lf = ctx.add_level(lev_lf, P=False)
+        # the batch of mesh l: fine draws of pair l, then the coarse draws of pair l+1
+        parts = [xi_uniform(cfg.seed, l, cfg.samples[l], cfg.K)]
+        if l + 1 < cfg.levels:
+            parts.append(xi_uniform(cfg.seed, l + 1, cfg.samples[l + 1], cfg.K))
+        xi_np = np.concatenate(parts)
+        S = xi_np.shape[0]
+        xi = torch.from_numpy(xi_np).cuda()
+        row = {"level": l, "S": S, "n_free": h_lts.info["n_free"], "n_R": h_lts.info["n_R"], "p": cfg.p}
+        for name, h in (("lts", h_lts), ("lf", h_lf)):
+            q = torch.zeros(S, dtype=torch.float64, device="cuda")
+            d = h.desc(cfg.precision)
+            with torch.cuda.stream(st):
+                lflts.lflts_solve(ctx.h, d, xi, S, q, None, lflts.LFLTS_MEM_DEVICE, st.cuda_stream)  # tune, capture
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                lflts.lflts_solve(ctx.h, d, xi, S, q, None, lflts.LFLTS_MEM_DEVICE, st.cuda_stream)
+                e1.record(st)
+            torch.cuda.synchronize()
+            row["t_" + name] = e0.elapsed_time(e1) * 1e-3
+            row["units_" + name] = S * costmodel.solve_work(h.n_steps if name == "lts" else h_lts.n_steps,
+                                                             h.info["n_free"], h_lts.info["n_R"], cfg.p, name)
+            Q[(l, name)] = q.cpu().numpy()
+        row["work_ratio_lf_over_lts"] = row["units_lf"] / row["units_lts"]
+        row["time_ratio_lf_over_lts"] = row["t_lf"] / row["t_lts"]
+        row["mean_abs_dQ_lf_vs_lts"] = float(np.abs(Q[(l, "lf")] - Q[(l, "lts")]).mean())
+        out["levels"].append(row)
+    # MLMC speed-up (Prop. 3.2) with V_l from the batch and per-sample pair costs
+    V, Ct, Cu = {"lf": [], "lts": []}, {"lf": [], "lts": []}, {"lf": [], "lts": []}
+    for name in ("lf", "lts"):
+        for i, row in enumerate(out["levels"]):
+            l = row["level"]
+            n = cfg.samples[l]
+            qf = Q[(l, name)][:n]
+            dq = qf - Q[(l - 1, name)][cfg.samples[l - 1]:cfg.samples[l - 1] + n] if l > 0 else qf
+            V[name].append(float(np.var(dq, ddof=1)))
+            ct = row["t_" + name] / row["S"] + (out["levels"][i - 1]["t_" + name] / out["levels"][i - 1]["S"] if l else 0)
+            cu = row["units_" + name] / row["S"] + (out["levels"][i - 1]["units_" + name] / out["levels"][i - 1]["S"] if l else 0)
+            Ct[name].append(ct)
+            Cu[name].append(cu)
+    out["V_lts"], out["V_lf"] = V["lts"], V["lf"]
+    out["S_prop32_measured_time"] = costmodel.speedup_S(V["lts"], Ct["lf"], Ct["lts"])
+    out["S_prop32_work_units"] = costmodel.speedup_S(V["lts"], Cu["lf"], Cu["lts"])
+    ctx.close()
+    print(json.dumps(out), flush=True)
 
 
 def run_profile_case(args):
@@ -471,8 +540,12 @@ def main():
                     help="run only a few steps of one mesh solve (for ncu captures)")
     ap.add_argument("--profile-steps", type=int, default=4)
     ap.add_argument("--profile-samples", type=int, default=0)
+    ap.add_argument("--lts-vs-lf", action="store_true", help="compare LF-LTS with standard leapfrog")
+    ap.add_argument("--lts-vs-lf-levels", type=int, default=2)
     args = ap.parse_args()
-    if args.profile_case >= 0:
+    if args.lts_vs_lf:
+        run_lts_vs_lf(args)
+    elif args.profile_case >= 0:
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -143,6 +143,15 @@ int lflts_lts_constants(int p, double nu, double dt, double* out);
 int lflts_field_add(lflts_ctx* ctx, int mesh_id, const double* values, int* field_id);
 
 /*
+ * Register a load vector F (the space part of the forcing f(x,t) =
+ * r(t) f(x), F_i = (f, phi_i); a point source at x_s has F_i = phi_i(x_s)) on
+ * a mesh: nodes [n] node indices, weights [n] FP64.  It enters Alg. 2 through
+ * w_n = A (I - P) z_n - F~(t_n), frozen over the inner substeps of a step.
+ */
+int lflts_source_add(lflts_ctx* ctx, int mesh_id, const int32_t* nodes, const double* weights,
+                     int64_t n, int* source_id);
+
+/*
  * Register a linear QoI Q(u) = sum_k g[k] u[idx[k]] on a mesh (Sec. 2.1,
  * V = R).  idx [nnz] int32 node indices, g [nnz] FP64 weights.
  */
@@ -160,6 +169,10 @@ typedef struct {
   double nu;        /* stabilisation parameter, 0 <= nu <= 1                  */
   double dt;        /* coarse time step                                       */
   int64_t n_steps;  /* N >= 1 steps; the QoI is taken at t_N = N dt           */
+  int source_id;    /* load vector from lflts_source_add, or -1 (f = 0)       */
+  double src_f0;    /* Ricker wavelet of the source: F(t) = amp r(t) F,       */
+  double src_t0;    /*   r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2) */
+  double src_amp;
 } lflts_solve_desc;
 
 /*

@@ -22,13 +22,15 @@ from __future__ import annotations
 import numpy as np
 
 from .fem import coefficient, stiffness
-from .lts import Problem, lts_constants, qoi, solve_qoi
+from .lts import Problem, lts_constants, qoi, solve_qoi, source_forcing
 
 
-def _tangent_inner(q0, dq0, A, dA, Pd, dt, C):
+def _tangent_inner(q0, dq0, A, dA, Pd, dt, C, Ft=None):
     p, omega, delta = C["p"], C["omega"], C["delta"]
     tau2 = (dt / p) ** 2
     w = A @ ((1.0 - Pd) * q0)
+    if Ft is not None:
+        w = w - Ft  # the forcing does not depend on xi: it has no tangent
     dw = dA @ ((1.0 - Pd) * q0) + A @ ((1.0 - Pd) * dq0)
     a0 = 0.5 * tau2 * (2.0 * p**2 / (omega * delta))
     q_prev, dq_prev = q0, dq0
@@ -56,15 +58,17 @@ def tangent_gradient(level: dict, xi) -> tuple:
     dt, N, p, nu = level["dt"], level["n_steps"], level["p"], level["nu"]
     C = lts_constants(p, nu)
     z0 = pb.to_z(level["u0"])
+    F = source_forcing(pb, m.n_nodes, level.get("source"))
+    Ft = (lambda n: F(n * dt)) if F is not None else (lambda n: None)
     grads = []
     zN = None
     for k in range(psi.shape[1]):
         Kk = stiffness(m.xy, m.tri, c2 * psi[:, k])[free][:, free]
         dA = Kk.multiply(s[:, None]).multiply(s[None, :]).tocsr()
         z_prev, dz_prev = z0, np.zeros_like(z0)
-        z, dz = _tangent_inner(z0, dz_prev, pb.A, dA, pb.Pd, dt, C)
-        for _ in range(1, N):
-            q, dq = _tangent_inner(z, dz, pb.A, dA, pb.Pd, dt, C)
+        z, dz = _tangent_inner(z0, dz_prev, pb.A, dA, pb.Pd, dt, C, Ft(0))
+        for n in range(1, N):
+            q, dq = _tangent_inner(z, dz, pb.A, dA, pb.Pd, dt, C, Ft(n))
             z_prev, z, dz_prev, dz = z, -z_prev + 2.0 * q, dz, -dz_prev + 2.0 * dq
         zN = z
         grads.append(qoi(pb.to_u(dz), level["qoi_idx"], level["qoi_w"]))

@@ -153,16 +153,33 @@ class Problem:
         return u
 
 
+def ricker(t, f0, t0):
+    """Ricker wavelet r(t) = (1 - 2 pi^2 f0^2 (t - t0)^2) exp(-pi^2 f0^2 (t - t0)^2)."""
+    a = (np.pi * f0 * (t - t0)) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def source_forcing(pb, n_nodes, source):
+    """F~(t) = M^{-1/2} F(t), F(t) = amp r(t) F_space, as a callable of t (z-form)."""
+    if source is None:
+        return None
+    F = np.zeros(n_nodes)
+    np.add.at(F, np.asarray(source["nodes"]), np.asarray(source["weights"], dtype=np.float64))
+    Ft = F[pb.free] / pb.sqrt_m
+    return lambda t: source["amp"] * ricker(t, source["f0"], source["t0"]) * Ft
+
+
 def solve_sample(xy, tri, dirichlet, P, psi, xi, u0, dt, n_steps, p, nu, v0=None,
-                 scheme="lts"):
+                 scheme="lts", source=None):
     """u_N (all nodes) for one draw xi: the per-sample hot path of Alg. 1."""
     pb = Problem(xy, tri, dirichlet, P, psi, xi)
     z0 = pb.to_z(u0)
     zv0 = pb.to_z(v0) if v0 is not None else np.zeros_like(z0)
+    F = source_forcing(pb, xy.shape[0], source)
     if scheme == "lts":
-        zN = march_lts(pb.A, pb.Pd, z0, zv0, dt, n_steps, p, nu)
+        zN = march_lts(pb.A, pb.Pd, z0, zv0, dt, n_steps, p, nu, F=F)
     elif scheme == "lf":
-        zN = march_lf(pb.A, z0, zv0, dt, n_steps)
+        zN = march_lf(pb.A, z0, zv0, dt, n_steps, F=F)
     else:
         raise ValueError(scheme)
     return pb.to_u(zN)
@@ -177,5 +194,6 @@ def solve_qoi(level: dict, xi, scheme="lts") -> float:
     """Q_l(omega) for one draw on one level (dict as built by workload)."""
     m = level["mesh"]
     u = solve_sample(m.xy, m.tri, m.dirichlet, m.P, level["psi"], xi, level["u0"],
-                     level["dt"], level["n_steps"], level["p"], level["nu"], scheme=scheme)
+                     level["dt"], level["n_steps"], level["p"], level["nu"], scheme=scheme,
+                     source=level.get("source"))
     return qoi(u, level["qoi_idx"], level["qoi_w"])

@@ -45,5 +45,6 @@ def lflts_qoi(ctx: "lflts.Context", level: "lflts.LevelHandle", xi: torch.Tensor
     if xi.dtype != torch.float64 or not xi.is_cuda or xi.dim() != 2:
         raise ValueError("xi must be a CUDA float64 tensor [S, K]")
     d = level.desc(precision)
-    desc_tuple = (d.mesh_id, d.qoi_id, d.u0_field, d.v0_field, d.precision, d.p, d.nu, d.dt, d.n_steps)
+    desc_tuple = (d.mesh_id, d.qoi_id, d.u0_field, d.v0_field, d.precision, d.p, d.nu, d.dt, d.n_steps,
+                  d.source_id, d.src_f0, d.src_t0, d.src_amp)
     return _LFLTSQoI.apply(xi, ctx.h, desc_tuple, int(ckpt_every))

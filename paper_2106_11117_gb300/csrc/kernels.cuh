@@ -147,14 +147,15 @@ k_edge_weights(int64_t n_edges, int S, int SB, const int2* __restrict__ ee,
 }
 
 // ---------------------------------------------------------------------------
-// Coarse part of one step, all free nodes: g = a(u_n) = M^-1 K u_n.
+// Coarse part of one step, all free nodes: g = a(u_n) - M^-1 F(t_n).
 //   outside R: d += -kappa*gamma*g, u_next = u_n + d
 //   inside  R: store g
 // ---------------------------------------------------------------------------
 template <typename Real, int VEC, int MINB = 1>
 __global__ void __launch_bounds__(256, MINB)
 k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real* __restrict__ u,
-         Real* __restrict__ u_next, Real* __restrict__ d, Real* __restrict__ g, Real kappa_gamma) {
+         Real* __restrict__ u_next, Real* __restrict__ d, Real* __restrict__ g, Real kappa_gamma,
+         const Real* __restrict__ fw, Real famp) {
   const Lane l = lane_of(SB);
   const int s0 = l.sv * VEC;
   if (s0 >= S) return;
@@ -192,9 +193,11 @@ k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real*
 #pragma unroll
       for (int k = 0; k < VEC; ++k) acc[k] = fma(wo.v[k], uo.v[k] - ui.v[k], acc[k]);
     }
+    // g = a(u_n) - M^-1 F(t_n): fw = M^-1 F (sample independent), famp = r(t_n)
+    const Real fi = fw ? famp * fw[i] : Real(0);
     Pack<Real, VEC> gi;
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) gi.v[k] = mi * acc[k];
+    for (int k = 0; k < VEC; ++k) gi.v[k] = mi * acc[k] - fi;
     if (outside) {
       Pack<Real, VEC> un;
 #pragma unroll

@@ -57,6 +57,12 @@ struct Field {
   double* v64 = nullptr;
 };
 
+struct Source {
+  int mesh;
+  float* fw32 = nullptr;   // M^-1 F on the free nodes (internal order)
+  double* fw64 = nullptr;
+};
+
 struct Qoi {
   int mesh;
   int nnz;
@@ -70,7 +76,8 @@ struct GraphKey {
   double nu, dt;
   int64_t n_steps, S;
   const void *xi, *Q, *uN, *ua, *ub, *d, *g, *r0, *r1, *r2, *W, *xipad, *qps, *qpc;
-  int vec, cps;
+  int vec, cps, source;
+  double f0, t0, famp;
   bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
@@ -105,6 +112,7 @@ struct lflts_ctx {
   std::vector<std::unique_ptr<MeshGPU>> meshes;
   std::vector<Field> fields;
   std::vector<Qoi> qois;
+  std::vector<Source> sources;
   std::vector<std::unique_ptr<Workspace>> ws;
   std::unique_ptr<Workspace> gws;   // forward buffers of lflts_grad_xi
   std::unique_ptr<GradBufs> gb;     // adjoint buffers of lflts_grad_xi
@@ -282,6 +290,7 @@ struct Sel<float> {
   static const float* field(const Field& f) { return f.v32; }
   static const float* eg(const MeshGPU& m) { return m.eg32; }
   static const float* psi(const MeshGPU& m) { return m.psi32; }
+  static const float* fw(const Source& s) { return s.fw32; }
 };
 template <>
 struct Sel<double> {
@@ -291,6 +300,7 @@ struct Sel<double> {
   static const double* field(const Field& f) { return f.v64; }
   static const double* eg(const MeshGPU& m) { return m.eg64; }
   static const double* psi(const MeshGPU& m) { return m.psi64; }
+  static const double* fw(const Source& s) { return s.fw64; }
 };
 
 // Geometry of the node/edge kernels: SB lanes of VEC samples per node.
@@ -314,6 +324,15 @@ struct Stepper {
   Real* g = nullptr;
   Real* rbuf[3] = {nullptr, nullptr, nullptr};
   bool minb6 = false;
+  const Real* fw = nullptr;  // M^-1 F or null
+  double f0 = 0, t0 = 0, famp = 0, dt = 0;
+
+  // r(t) of the Ricker wavelet times the amplitude
+  Real source_amp(double t) const {
+    if (!fw) return Real(0);
+    const double a = M_PI * M_PI * f0 * f0 * (t - t0) * (t - t0);
+    return (Real)(famp * (1.0 - 2.0 * a) * std::exp(-a));
+  }
 
   Stepper(lflts_ctx* c_, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R_, int64_t S_, const Real* W_,
           Real* g_, Real* r0, Real* r1, Real* r2, int shape = 16)
@@ -321,6 +340,13 @@ struct Stepper {
     // shape = CTAs per SM target, +100 for the register-capped kernels
     minb6 = shape >= 100;
     const int cta_per_sm = shape % 100;
+    dt = ds.dt;
+    if (ds.source_id >= 0) {
+      fw = Sel<Real>::fw(c->sources[ds.source_id]);
+      f0 = ds.src_f0;
+      t0 = ds.src_t0;
+      famp = ds.src_amp;
+    }
     const HostMesh& h = mg.h;
     rbuf[0] = r0;
     rbuf[1] = r1;
@@ -336,14 +362,15 @@ struct Stepper {
 
   // u_next = 2 T u_cur - u_prev in increments: d += kappa r_p, u_next = u_cur + d.
   // minb6: the register-capped instantiation (at least 6 CTAs of 256 per SM).
-  int step(const Real* uc, Real* un, Real* d, Real kappa, cudaStream_t st) {
+  int step(const Real* uc, Real* un, Real* d, Real kappa, cudaStream_t st, int64_t n = 0) {
     {
       Prof pr(c, st);
       const Real kg = (Real)(double(kappa) * gamma);
+      const Real fa = source_amp(double(n) * dt);
       if (minb6)
-        k_coarse<Real, VEC, 6><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg);
+        k_coarse<Real, VEC, 6><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg, fw, fa);
       else
-        k_coarse<Real, VEC, 1><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg);
+        k_coarse<Real, VEC, 1><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg, fw, fa);
       LF_CUDA(c, cudaGetLastError());
       pr.end(LFLTS_KERNEL_COARSE, coarse_bytes);
     }
@@ -398,7 +425,7 @@ int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n
   Real* d = static_cast<Real*>(ws.d.p);
   const int64_t N = n_steps >= 0 ? n_steps : ds.n_steps;
   for (int64_t n = 0; n < N; ++n) {
-    LF_TRY(stp.step(uc, un, d, (n == 0) ? Real(1) : Real(2), st));
+    LF_TRY(stp.step(uc, un, d, (n == 0) ? Real(1) : Real(2), st, n));
     std::swap(uc, un);
   }
   uc_out = uc;
@@ -595,6 +622,10 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   key.qpc = ws.qpc.p;
   key.vec = vec;
   key.cps = cps;
+  key.source = ds.source_id;
+  key.f0 = ds.src_f0;
+  key.t0 = ds.src_t0;
+  key.famp = ds.src_amp;
   for (auto& ge : ws.graphs)
     if (ge.key == key) {
       LF_CUDA(c, cudaGraphLaunch(ge.exec, st));
@@ -653,6 +684,10 @@ int check_desc(lflts_ctx* c, const lflts_solve_desc* ds) {
   if (!(ds->nu >= 0.0 && ds->nu <= 1.0)) return fail(c, LFLTS_ERR_ARG, "solve: nu must be in [0, 1]");
   if (!(ds->dt > 0.0) || !std::isfinite(ds->dt)) return fail(c, LFLTS_ERR_ARG, "solve: dt must be positive");
   if (ds->n_steps < 1) return fail(c, LFLTS_ERR_ARG, "solve: n_steps must be >= 1");
+  if (ds->source_id >= 0 && (ds->source_id >= (int)c->sources.size() || c->sources[ds->source_id].mesh != ds->mesh_id))
+    return fail(c, LFLTS_ERR_ARG, "solve: source_id does not belong to the mesh");
+  if (ds->source_id >= 0 && !(std::isfinite(ds->src_f0) && std::isfinite(ds->src_t0) && std::isfinite(ds->src_amp)))
+    return fail(c, LFLTS_ERR_ARG, "solve: non-finite source parameters");
   return 0;
 }
 
@@ -763,7 +798,7 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
       LF_CUDA(c, cudaMemcpyAsync(ckpt + (2 * (n / k)) * sn, uc, state, cudaMemcpyDeviceToDevice, st));
       LF_CUDA(c, cudaMemcpyAsync(ckpt + (2 * (n / k) + 1) * sn, d, state, cudaMemcpyDeviceToDevice, st));
     }
-    LF_TRY(stp.step(uc, un, d, (n == 0) ? Real(1) : Real(2), st));
+    LF_TRY(stp.step(uc, un, d, (n == 0) ? Real(1) : Real(2), st, n));
     std::swap(uc, un);
   }
   {  // QoI of u_N
@@ -815,13 +850,14 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
     LF_CUDA(c, cudaMemcpyAsync(segU, ckpt + (2 * seg) * sn, state, cudaMemcpyDeviceToDevice, st));
     LF_CUDA(c, cudaMemcpyAsync(d, ckpt + (2 * seg + 1) * sn, state, cudaMemcpyDeviceToDevice, st));
     for (int64_t n = n0; n + 1 < n1; ++n)
-      LF_TRY(stp.step(segU + (n - n0) * sn, segU + (n - n0 + 1) * sn, d, (n == 0) ? Real(1) : Real(2), st));
+      LF_TRY(stp.step(segU + (n - n0) * sn, segU + (n - n0 + 1) * sn, d, (n == 0) ? Real(1) : Real(2), st, n));
     for (int64_t n = n1 - 1; n >= n0; --n) {
       const Real kappa = (n == 0) ? Real(1) : Real(2);
       const Real* u_n = segU + (n - n0) * sn;
       if (n_R > 0) {
         // (i) g = a(u_n) on R; (ii) r_2 .. r_{p-1} of the inner recursion
-        k_coarse<Real, VEC><<<gR.grid, 256, 0, st>>>(mdR, (int)S, gR.SB, W, u_n, nullptr, nullptr, gs, Real(0));
+        k_coarse<Real, VEC><<<gR.grid, 256, 0, st>>>(mdR, (int)S, gR.SB, W, u_n, nullptr, nullptr, gs, Real(0),
+                                                      stp.fw, stp.source_amp(double(n) * ds.dt));
         LF_CUDA(c, cudaGetLastError());
         c->launches++;
         for (int m = 1; m <= p - 2; ++m) {
@@ -857,7 +893,11 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
       c->launches++;
       // (v) nu_n = 2 T nu_{n+1} - nu_{n+2}
       if (n > 0) {
-        LF_TRY(stp.step(vc, vn, dv, Real(2), st));
+        const Real* fw_saved = stp.fw;
+        stp.fw = nullptr;  // the adjoint recursion has no forcing
+        const int rc = stp.step(vc, vn, dv, Real(2), st);
+        stp.fw = fw_saved;
+        LF_TRY(rc);
         std::swap(vc, vn);
       }
     }
@@ -1077,6 +1117,29 @@ int lflts_field_add(lflts_ctx* c, int mesh_id, const double* values, int* field_
   return LFLTS_OK;
 }
 
+int lflts_source_add(lflts_ctx* c, int mesh_id, const int32_t* nodes, const double* weights, int64_t n,
+                     int* source_id) {
+  if (!c || !source_id || n < 1 || !nodes || !weights) return LFLTS_ERR_ARG;
+  if (mesh_id < 0 || mesh_id >= (int)c->meshes.size()) return fail(c, LFLTS_ERR_ARG, "source_add: bad mesh_id");
+  LF_TRY(set_device(c));
+  const HostMesh& h = c->meshes[mesh_id]->h;
+  std::vector<double> fw64(std::max<int64_t>(h.n_free, 1), 0.0);
+  for (int64_t k = 0; k < n; ++k) {
+    if (nodes[k] < 0 || nodes[k] >= h.n_nodes) return fail(c, LFLTS_ERR_ARG, "source_add: node out of range");
+    if (!std::isfinite(weights[k])) return fail(c, LFLTS_ERR_ARG, "source_add: non-finite weight");
+    const int32_t nn = h.old2new[nodes[k]];
+    if (nn < h.n_free) fw64[nn] += weights[k] * h.minv[nn];  // M^-1 F; Dirichlet rows dropped
+  }
+  std::vector<float> fw32(fw64.begin(), fw64.end());
+  Source src;
+  src.mesh = mesh_id;
+  LF_TRY(upload(c, &src.fw64, fw64.data(), fw64.size()));
+  LF_TRY(upload(c, &src.fw32, fw32.data(), fw32.size()));
+  *source_id = static_cast<int>(c->sources.size());
+  c->sources.push_back(src);
+  return LFLTS_OK;
+}
+
 int lflts_qoi_add(lflts_ctx* c, int mesh_id, const int32_t* idx, const double* g, int64_t nnz, int* qoi_id) {
   if (!c || !qoi_id || (nnz > 0 && (!idx || !g)) || nnz < 0 || nnz >= INT_MAX) return LFLTS_ERR_ARG;
   if (mesh_id < 0 || mesh_id >= (int)c->meshes.size()) return fail(c, LFLTS_ERR_ARG, "qoi_add: bad mesh_id");
@@ -1171,7 +1234,8 @@ int lflts_run_pairs(lflts_ctx* c, const lflts_pair_job* jobs, int n_jobs, int me
   auto key_eq = [](const lflts_solve_desc& a, const lflts_solve_desc& b) {
     return a.mesh_id == b.mesh_id && a.qoi_id == b.qoi_id && a.u0_field == b.u0_field &&
            a.v0_field == b.v0_field && a.precision == b.precision && a.p == b.p && a.nu == b.nu &&
-           a.dt == b.dt && a.n_steps == b.n_steps;
+           a.dt == b.dt && a.n_steps == b.n_steps && a.source_id == b.source_id && a.src_f0 == b.src_f0 &&
+           a.src_t0 == b.src_t0 && a.src_amp == b.src_amp;
   };
   auto add_member = [&](const lflts_solve_desc& ds, int j, bool fine, int64_t S) {
     for (auto& gr : groups)

@@ -37,6 +37,7 @@ EXPORTED = [
     "lflts_qoi_add", "lflts_solve", "lflts_level_sums", "lflts_run_pairs",
     "lflts_profile_enable", "lflts_profile_reset", "lflts_profile_read", "lflts_launch_count",
     "lflts_qoi_reduce_noalloc", "lflts_grad_xi", "lflts_set_option", "lflts_get_stats",
+    "lflts_source_add",
 ]
 LFLTS_OPT_GRAPHS = 1
 LFLTS_OPT_AUTOTUNE = 2
@@ -55,7 +56,14 @@ class LfltsError(RuntimeError):
 class SolveDesc(C.Structure):
     _fields_ = [("mesh_id", C.c_int), ("qoi_id", C.c_int), ("u0_field", C.c_int),
                 ("v0_field", C.c_int), ("precision", C.c_int), ("p", C.c_int),
-                ("nu", C.c_double), ("dt", C.c_double), ("n_steps", C.c_int64)]
+                ("nu", C.c_double), ("dt", C.c_double), ("n_steps", C.c_int64),
+                ("source_id", C.c_int), ("src_f0", C.c_double), ("src_t0", C.c_double),
+                ("src_amp", C.c_double)]
+
+    def __init__(self, *args, **kw):
+        super().__init__(*args, **kw)
+        if len(args) < 10 and "source_id" not in kw:
+            self.source_id = -1
 
 
 class PairJob(C.Structure):
@@ -101,6 +109,7 @@ def load(path: str | None = None):
         "lflts_qoi_reduce_noalloc": (i32, [vp, vp, i32, i64, i64, vp, vp, i64, vp, vp]),
         "lflts_grad_xi": (i32, [vp, C.POINTER(SolveDesc), vp, i64, i32, vp, vp, i32, vp]),
         "lflts_set_option": (i32, [vp, i32, i64]),
+        "lflts_source_add": (i32, [vp, i32, vp, vp, i64, C.POINTER(i32)]),
         "lflts_get_stats": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -201,6 +210,14 @@ def lflts_field_add(ctx, mesh_id, values):
     return fid.value
 
 
+def lflts_source_add(ctx, mesh_id, nodes, weights):
+    nodes = np.ascontiguousarray(nodes, dtype=np.int32)
+    weights = np.ascontiguousarray(weights, dtype=np.float64)
+    sid = C.c_int()
+    _check(ctx, load().lflts_source_add(ctx, mesh_id, _ptr(nodes), _ptr(weights), nodes.shape[0], C.byref(sid)))
+    return sid.value
+
+
 def lflts_qoi_add(ctx, mesh_id, idx, g):
     idx = np.ascontiguousarray(idx, dtype=np.int32)
     g = np.ascontiguousarray(g, dtype=np.float64)
@@ -277,11 +294,12 @@ class LevelHandle:
     p: int
     nu: float
     info: dict
+    source: tuple = (-1, 0.0, 0.0, 0.0)  # (source_id, f0, t0, amplitude)
 
     def desc(self, precision: int, p: int | None = None) -> SolveDesc:
         return SolveDesc(self.mesh_id, self.qoi_id, self.u0_field, -1, int(precision),
                          int(self.p if p is None else p), float(self.nu), float(self.dt),
-                         int(self.n_steps))
+                         int(self.n_steps), *self.source)
 
 
 class Context:
@@ -308,8 +326,13 @@ class Context:
         mid = lflts_mesh_add(self.h, m.xy, m.tri, m.dirichlet, m.P if P else None, level["psi"])
         qid = lflts_qoi_add(self.h, mid, level["qoi_idx"], level["qoi_w"])
         fid = lflts_field_add(self.h, mid, level["u0"])
+        src = (-1, 0.0, 0.0, 0.0)
+        if level.get("source") is not None:
+            s_ = level["source"]
+            sid = lflts_source_add(self.h, mid, s_["nodes"], s_["weights"])
+            src = (sid, float(s_["f0"]), float(s_["t0"]), float(s_["amp"]))
         return LevelHandle(mid, qid, fid, level["dt"], level["n_steps"], level["p"], level["nu"],
-                           lflts_mesh_info(self.h, mid))
+                           lflts_mesh_info(self.h, mid), src)
 
     def grad(self, lv: LevelHandle, xi, precision=64, ckpt_every=16):
         """Host convenience: xi [S, K] -> (Q [S], dQ/dxi [S, K])."""

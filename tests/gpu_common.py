@@ -17,7 +17,7 @@ def small_level(n=12, p=3, K=4, box=(0.35, 0.65, 0.35, 0.65), T=0.6, nu=0.01,
             "qoi_idx": idx, "qoi_w": g, "dt": dt, "n_steps": n_steps, "p": p, "nu": nu, "T": T}
 
 
-def oracle_run(level, xi, scheme="lts", P=True, p=None, v0=None):
+def oracle_run(level, xi, scheme="lts", P=True, p=None, v0=None, source=None):
     """(Q [S], u_N [n_nodes, S]) from the FP64 oracle, one sample at a time."""
     m = level["mesh"]
     Pm = m.P if P else np.zeros(m.n_nodes, np.uint8)
@@ -25,7 +25,7 @@ def oracle_run(level, xi, scheme="lts", P=True, p=None, v0=None):
     for x in xi:
         us.append(solve_sample(m.xy, m.tri, m.dirichlet, Pm, level["psi"], x, level["u0"],
                                level["dt"], level["n_steps"], level["p"] if p is None else p,
-                               level["nu"], v0=v0, scheme=scheme))
+                               level["nu"], v0=v0, scheme=scheme, source=source))
     U = np.stack(us, axis=1)
     Q = level["qoi_w"] @ U[level["qoi_idx"]]
     return Q, U

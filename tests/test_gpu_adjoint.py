@@ -101,3 +101,16 @@ def test_autograd_function(lf, ctx):
     np.testing.assert_allclose(xi.grad.cpu().numpy(), w.cpu().numpy()[:, None] * G, rtol=1e-14, atol=1e-300)
     Qh = ctx.solve(h, xi_np, precision=64)
     np.testing.assert_array_equal(Q.detach().cpu().numpy(), Qh)
+
+
+def test_adjoint_with_point_source(lf, ctx):
+    from workload import point_source
+    lev = small_level(n=10, p=3, K=3, T=0.3)
+    nodes, w = point_source(lev["mesh"], (0.52, 0.49))
+    lev = dict(lev, source={"nodes": nodes, "weights": w, "f0": 8.0, "t0": 0.12, "amp": 1.5})
+    xi = draws(3, 3, seed=31)
+    h = ctx.add_level(lev)
+    Qo, Go = _oracle(lev, xi)
+    Q, G = ctx.grad(h, xi, precision=64, ckpt_every=3)
+    assert rel_err(Q, Qo) <= 1e-12
+    assert rel_err(G, Go) <= 1e-9, rel_err(G, Go)

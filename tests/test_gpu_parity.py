@@ -218,3 +218,21 @@ def test_profiling_counters(lf, ctx):
     assert inn["launches"] == h.n_steps * 3
     assert co["ms"] > 0 and inn["alg_bytes"] > 0
     assert lf.lflts_launch_count(ctx.h) - n0 == 3 + h.n_steps * 4 + 2
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_ricker_point_source_matches_oracle(lf, ctx, precision):
+    """Forcing f = r(t) delta(x - x_s) (Ricker wavelet), entering Alg. 2 through
+    w_n and frozen over the inner substeps."""
+    from workload import point_source
+    lev = small_level(n=12, p=3, K=4)
+    nodes, w = point_source(lev["mesh"], (0.5, 0.47))
+    lev = dict(lev, source={"nodes": nodes, "weights": w, "f0": 6.0, "t0": 0.2, "amp": 2.0},
+               u0=0.0 * lev["u0"])
+    xi = draws(6, 4, seed=17)
+    Qo, Uo = oracle_run(lev, xi, source=lev["source"])
+    h = ctx.add_level(lev)
+    Q, U = ctx.solve(h, xi, precision=precision, state=True)
+    assert np.abs(Uo).max() > 1e-3
+    assert rel_err(U, Uo) <= TOL_U[precision]
+    assert rel_err(Q, Qo) <= TOL_Q[precision]

@@ -211,3 +211,42 @@ def test_lts_initial_velocity_start():
     errs = [np.linalg.norm(march_lts(pb.A, pb.Pd, z0, zv, T / n, n, 2, 0.01) - zex)
             for n in (20, 40, 80)]
     assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
+
+
+# ----------------------------------------------------------------- forcing
+@pytest.mark.parametrize("lts", [False, True])
+def test_constant_forcing_closed_form(lts):
+    """Constant modal forcing F = f M phi from rest: the discrete solution is
+    c_n = (f / lam)(1 - cos(n Theta)) phi with cos Theta = 1 - dt^2 lam / 2 (LF,
+    P = 0) or T_p(delta - dt^2 lam / omega) / T_p(delta) (LTS, P = I): the
+    step is affine with fixed point f / lam (where w_n + A P q_0 = 0)."""
+    from oracle.fem import lumped_mass
+    from oracle.lts import solve_sample
+    n = 16
+    m = square_mesh(n)
+    h = 1.0 / n
+    phi = np.sin(np.pi * m.xy[:, 0]) * np.sin(2 * np.pi * m.xy[:, 1])
+    lam = 4 / h**2 * (math.sin(math.pi * h / 2) ** 2 + math.sin(math.pi * h) ** 2)
+    f = 3.0
+    mass = lumped_mass(m.xy, m.tri)
+    free = np.nonzero(~m.dirichlet.astype(bool))[0]
+    src = {"nodes": free, "weights": f * mass[free] * phi[free], "f0": 0.0, "t0": 0.0, "amp": 1.0}
+    dt, N, p, nu = 0.02, 37, 3, 0.01
+    Pm = (~m.dirichlet.astype(bool)).astype(np.uint8) if lts else np.zeros(m.n_nodes, np.uint8)
+    u = solve_sample(m.xy, m.tri, m.dirichlet, Pm, np.zeros((m.n_tri, 1)), np.zeros(1),
+                     np.zeros(m.n_nodes), dt, N, p, nu, source=src)
+    if lts:
+        C = lts_constants(p, nu)
+        S = _Tp(p, C["delta"] - dt * dt * lam / C["omega"]) / _Tp(p, C["delta"])
+    else:
+        S = 1 - dt * dt * lam / 2
+    expect = f / lam * (1 - math.cos(N * math.acos(S))) * phi
+    assert np.abs(u - expect).max() < 1e-12 * np.abs(expect).max()
+
+
+def test_ricker_wavelet_values():
+    from oracle.lts import ricker
+    assert ricker(0.3, 10.0, 0.3) == 1.0
+    # zero crossings at |t - t0| = 1 / (sqrt(2) pi f0)
+    assert abs(ricker(0.3 + 1 / (math.sqrt(2) * math.pi * 10.0), 10.0, 0.3)) < 1e-15
+    assert ricker(1.0, 0.0, 0.0) == 1.0

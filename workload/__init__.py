@@ -7,12 +7,14 @@ the box-average quantity of interest.  It contains none of the method's
 arithmetic (no mass or stiffness assembly, no time stepping, no MLMC
 estimator); those live independently in ``oracle/`` and in the CUDA library.
 """
-from .mesh import Mesh, square_mesh, refined_mask_from_elements
-from .fields import (psi_sine, xi_uniform, gaussian_bump, box_qoi_weights,
+from .mesh import Mesh, lshape_graded_mesh, square_mesh, refined_mask_from_elements
+from .fields import (point_source, psi_sine, xi_uniform, gaussian_bump, box_qoi_weights,
                      coarse_dt, SquareConfig, CONFIG_PLAIN, CONFIG_BATCHED,
-                     CONFIG_BANDWIDTH, CONFIG_ADJOINT, level_problem)
+                     CONFIG_BANDWIDTH, CONFIG_ADJOINT, level_problem, LShapeConfig,
+                     CONFIG_LSHAPE, lshape_level, lshape_steps, xi_gaussian)
 
-__all__ = ["Mesh", "square_mesh", "refined_mask_from_elements", "psi_sine",
+__all__ = ["Mesh", "square_mesh", "point_source", "refined_mask_from_elements", "psi_sine",
            "xi_uniform", "gaussian_bump", "box_qoi_weights", "coarse_dt",
            "SquareConfig", "CONFIG_PLAIN", "CONFIG_BATCHED",
-           "CONFIG_BANDWIDTH", "CONFIG_ADJOINT", "level_problem"]
+           "CONFIG_BANDWIDTH", "CONFIG_ADJOINT", "level_problem", "LShapeConfig",
+           "CONFIG_LSHAPE", "lshape_level", "lshape_steps", "xi_gaussian"]

@@ -27,7 +27,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .mesh import Mesh, square_mesh
+from .mesh import Mesh, lshape_graded_mesh, square_mesh
 
 
 # --------------------------------------------------------------------------
@@ -134,6 +134,23 @@ def box_qoi_weights(mesh: Mesh, box=(0.7, 0.8, 0.7, 0.8)):
     return idx, w[idx].astype(np.float64)
 
 
+def point_source(mesh: Mesh, xs):
+    """Load vector of a point source at xs: F_i = phi_i(xs), nonzero on the
+    three vertices of the triangle containing xs (barycentric coordinates)."""
+    xs = np.asarray(xs, dtype=np.float64)
+    V = mesh.xy[mesh.tri]
+    lo, hi = V.min(axis=1), V.max(axis=1)
+    cand = np.nonzero((lo[:, 0] <= xs[0]) & (hi[:, 0] >= xs[0]) & (lo[:, 1] <= xs[1]) & (hi[:, 1] >= xs[1]))[0]
+    for e in cand:
+        T = V[e]
+        M = np.array([[T[1, 0] - T[0, 0], T[2, 0] - T[0, 0]], [T[1, 1] - T[0, 1], T[2, 1] - T[0, 1]]])
+        l12 = np.linalg.solve(M, xs - T[0])
+        lam = np.array([1.0 - l12.sum(), l12[0], l12[1]])
+        if (lam >= -1e-12).all():
+            return mesh.tri[e].astype(np.int32), np.clip(lam, 0.0, 1.0)
+    raise ValueError("point outside the mesh")
+
+
 # --------------------------------------------------------------------------
 # time step and configurations
 # --------------------------------------------------------------------------
@@ -205,3 +222,81 @@ def level_problem(cfg: SquareConfig, level: int, n0: int | None = None) -> dict:
         "nu": cfg.nu,
         "T": cfg.T,
     }
+
+
+# --------------------------------------------------------------------------
+# graded L-shape workload with a Ricker source and Gaussian draws
+# --------------------------------------------------------------------------
+@dataclass(frozen=True)
+class LShapeConfig:
+    """L-shaped domain [-1,1]^2 minus [0,1]x[-1,0], mesh T_{m,s} graded toward the
+    reentrant corner (Sec. 3.5), m_l = m0 2^l, s = 2; the first q_l tiers are
+    refined and the LTS ratio is p_l = 2 q_l + 1 (the tier sizes grow like
+    2k - 1, so the coarse step is set by tier q_l + 1).  c^2 = exp(sum_k xi_k
+    psi_k), psi_k = sin(k pi (x+1)/2) sin(k pi (y+1)/2) / k^2, xi_k ~ N(0, sigma^2)
+    (unbounded: each draw gets its own time step), Ricker source at (-0.5, 0.5),
+    zero initial data, QoI = mean of u over [0.4, 0.6]^2 at T."""
+    name: str = "lshape-graded-s2-K16-ricker"
+    m0: int = 58
+    s: float = 2.0
+    q_levels: tuple = (1, 2, 4, 8)
+    K: int = 16
+    sigma: float = 0.5
+    samples: tuple = (4096, 1024, 256, 64)
+    T: float = 1.0
+    nu: float = 0.01
+    seed: int = 3
+    source_xy: tuple = (-0.5, 0.5)
+    f0: float = 10.0
+    qoi_box: tuple = (0.4, 0.6, 0.4, 0.6)
+    precision: int = 32
+
+    @property
+    def levels(self) -> int:
+        return len(self.q_levels)
+
+
+CONFIG_LSHAPE = LShapeConfig()
+
+
+def psi_sine_lshape(mesh: Mesh, K: int) -> np.ndarray:
+    c = centroids(mesh)
+    k = np.arange(1, K + 1, dtype=np.float64)
+    return (np.sin(np.pi * (c[:, :1] + 1) / 2 * k) * np.sin(np.pi * (c[:, 1:2] + 1) / 2 * k) / k**2)
+
+
+def xi_gaussian(seed: int, level: int, S: int, K: int, sigma: float, offset: int = 0) -> np.ndarray:
+    ss = np.random.SeedSequence([int(seed), int(level), 7])
+    gen = np.random.Generator(np.random.Philox(ss))
+    if offset:
+        gen.normal(0.0, sigma, size=(offset, K))
+    return gen.normal(0.0, sigma, size=(S, K)).astype(np.float64)
+
+
+def lshape_level(cfg: LShapeConfig, level: int, m0: int | None = None) -> dict:
+    m = (cfg.m0 if m0 is None else m0) * 2**level
+    q = cfg.q_levels[level]
+    mesh = lshape_graded_mesh(m, cfg.s, q)
+    V = mesh.xy[mesh.tri]
+    e = [np.linalg.norm(V[:, i] - V[:, (i + 1) % 3], axis=1) for i in range(3)]
+    a2 = np.abs((V[:, 1, 0] - V[:, 0, 0]) * (V[:, 2, 1] - V[:, 0, 1]) - (V[:, 2, 0] - V[:, 0, 0]) * (V[:, 1, 1] - V[:, 0, 1]))
+    r_in = a2 / (e[0] + e[1] + e[2])          # inradius = 2 area / perimeter
+    coarse = ~mesh.refined.astype(bool)
+    idx, g = box_qoi_weights(mesh, cfg.qoi_box)
+    nodes, w = point_source(mesh, cfg.source_xy)
+    return {"mesh": mesh, "psi": psi_sine_lshape(mesh, cfg.K), "u0": np.zeros(mesh.n_nodes),
+            "qoi_idx": idx, "qoi_w": g, "p": 2 * q + 1, "nu": cfg.nu, "T": cfg.T,
+            "h_min_coarse": float(2.0 * r_in[coarse].min()),
+            "source": {"nodes": nodes, "weights": w, "f0": cfg.f0, "t0": 1.2 / cfg.f0, "amp": 1.0}}
+
+
+def lshape_steps(level: dict, xi: np.ndarray, ladder: float = 1.25) -> np.ndarray:
+    """Per-draw step counts: dt(w) = 0.5 h_min / c_max(w) with the bound
+    c_max^2 <= exp(sum_k |xi_k| / k^2) of the draw, n = ceil(T / dt) rounded up
+    to a geometric ladder (ratio 1.25) so that draws fall into few buckets."""
+    k = np.arange(1, xi.shape[1] + 1, dtype=np.float64)
+    cmax = np.exp(0.5 * (np.abs(xi) / k**2).sum(axis=1))
+    n = np.ceil(level["T"] / (0.5 * level["h_min_coarse"] / cmax))
+    base = np.ceil(level["T"] / (0.5 * level["h_min_coarse"]))
+    j = np.ceil(np.log(n / base) / np.log(ladder) - 1e-12)
+    return np.maximum(np.ceil(base * ladder ** np.maximum(j, 0)), 1).astype(np.int64)

@@ -220,3 +220,59 @@ def square_mesh(n: int, box=None, p: int = 1, box_cells=None) -> Mesh:
     return Mesh(xy=xy, tri=tri, dirichlet=dirichlet, P=P, refined=refined,
                 H=1.0 / n, h_f=1.0 / L, p=p, box=snapped,
                 meta={"n": n, "box_cells": (I0, I1, J0, J1) if refine else None})
+
+
+def lshape_graded_mesh(m: int, s: float = 2.0, q: int = 1) -> Mesh:
+    """Graded mesh T_{m,s} of the L-shaped domain [-1,1]^2 minus [0,1]x[-1,0]
+    (Sec. 3.5): six triangles of equal area share the reentrant corner C =
+    (0,0); on every edge from C the m+1 layer points lie at |e| (k/m)^s,
+    k = 0..m, and the k+1 points of layer k inside each triangle are spread
+    uniformly, so each of the six triangles holds m^2 elements in m tiers.
+    The first q tiers (the elements touching layers < q) are the refined
+    region; P follows the same rule as for the square meshes."""
+    C = np.array([0.0, 0.0])
+    outer = [(0.0, -1.0), (-1.0, -1.0), (-1.0, 0.0), (-1.0, 1.0), (0.0, 1.0), (1.0, 1.0), (1.0, 0.0)]
+    t = (np.arange(m + 1) / m) ** s
+    pts, tris, tier = [], [], []
+    index = {}
+
+    def node(p):
+        key = (float(p[0]), float(p[1]))
+        if key not in index:
+            index[key] = len(pts)
+            pts.append(key)
+        return index[key]
+
+    for a, b in zip(outer[:-1], outer[1:]):
+        A, B = np.array(a), np.array(b)
+        ids = {}
+        for k in range(m + 1):
+            for j in range(k + 1):
+                w = (j / k) if k else 0.0
+                ids[(k, j)] = node(C + t[k] * ((1.0 - w) * (A - C) + w * (B - C)))
+        for k in range(1, m + 1):
+            for j in range(k):
+                tris.append((ids[(k - 1, min(j, k - 1))], ids[(k, j)], ids[(k, j + 1)]))
+                tier.append(k)
+            for j in range(k - 1):
+                tris.append((ids[(k - 1, j)], ids[(k, j + 1)], ids[(k - 1, j + 1)]))
+                tier.append(k)
+    xy = np.array(pts, dtype=np.float64)
+    tri = np.array(tris, dtype=np.int64)
+    V = xy[tri]
+    area2 = ((V[:, 1, 0] - V[:, 0, 0]) * (V[:, 2, 1] - V[:, 0, 1])
+             - (V[:, 2, 0] - V[:, 0, 0]) * (V[:, 1, 1] - V[:, 0, 1]))
+    flip = area2 < 0
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    tri = tri.astype(np.int32)
+    x, y = xy[:, 0], xy[:, 1]
+    eps = 1e-12
+    on_outer = (np.abs(x + 1) < eps) | (np.abs(x - 1) < eps) | (np.abs(y + 1) < eps) | (np.abs(y - 1) < eps)
+    on_notch = ((np.abs(x) < eps) & (y <= eps)) | ((np.abs(y) < eps) & (x >= -eps))
+    dirichlet = (on_outer | on_notch).astype(np.uint8)
+    tier = np.asarray(tier)
+    refined = (tier <= q).astype(np.uint8)
+    P = refined_mask_from_elements(tri, refined, xy.shape[0], dirichlet) if q > 0 else np.zeros(xy.shape[0], np.uint8)
+    h1 = (1.0 / m) ** s  # radial size of the first tier (on the unit spokes)
+    return Mesh(xy=xy, tri=tri, dirichlet=dirichlet, P=P, refined=refined, H=1.0 / m, h_f=h1, p=2 * q + 1,
+                box=None, meta={"m": m, "s": s, "q": q, "tier": tier})
