@@ -70,8 +70,14 @@ enum {
 enum {
   LFLTS_OPT_GRAPHS = 1,   /* 1 (default): solves on a non-default stream are captured once into a
                              CUDA graph and replayed while problem, batch and buffers are unchanged */
-  LFLTS_OPT_AUTOTUNE = 2  /* 1 (default): the first solve of a (mesh, S, precision, p) times the
-                             candidate launch shapes (draws per thread, CTAs per SM) and keeps the best */
+  LFLTS_OPT_AUTOTUNE = 2, /* 1 (default): the first solve of a (mesh, S, precision, p) times the
+                             candidate launch shapes (draws per thread, CTAs per SM, register cap)
+                             and keeps the best */
+  LFLTS_OPT_BLOCKED = 3,  /* 1: run the inner substeps in L2 blocks (block cores with halos of P
+                             nodes, draw slabs, all substeps of a block back to back; same results
+                             bit for bit, fewer DRAM bytes, more launches); 0 (default): one launch
+                             per substep over R */
+  LFLTS_OPT_BLOCK_BUDGET = 4 /* bytes of inner-loop working set per L2 block (default 40e6) */
 };
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -117,8 +123,9 @@ int lflts_mesh_info(lflts_ctx* ctx, int mesh_id, int64_t info[8]);
 /*
  * Internal node order of a mesh: new2old [n_nodes] receives, for each
  * internal position k, the caller's node index.  The order is
- * [P nodes | R \ P | other free nodes | Dirichlet nodes], each group in the
- * caller's order.  Works on host-only contexts (device -1).
+ * [P nodes | R \ P | other free nodes | Dirichlet nodes], each group in
+ * Morton (Z-curve) order of the node coordinates, ties in the caller's order.
+ * Works on host-only contexts (device -1).
  */
 int lflts_mesh_order(lflts_ctx* ctx, int mesh_id, int32_t* new2old);
 

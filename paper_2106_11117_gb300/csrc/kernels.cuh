@@ -219,18 +219,24 @@ k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real*
 // r_m = s_cur * cur, r_{m-1} = s_prev * prev (prev == nullptr: r_0 = 0).
 // LAST: fold r_p into d and u_next instead of storing it.
 // ---------------------------------------------------------------------------
-template <typename Real, int VEC, bool LAST, int MINB = 1>
+// LIST: the launch covers the nodes list[0..n_items) (an L2 block of the
+// inner loop) and the draws [s_lo, s_lo + s_cnt); otherwise all of R and all
+// draws.  The arithmetic per node and draw is the same either way.
+template <typename Real, int VEC, bool LAST, int MINB = 1, bool LIST = false>
 __global__ void __launch_bounds__(256, MINB)
 k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
         const Real* __restrict__ cur, Real s_cur, const Real* __restrict__ prev, Real s_prev,
         Real* __restrict__ r_next, const Real* __restrict__ g, const Real* __restrict__ u,
         Real* __restrict__ u_next, Real* __restrict__ d, Real one_plus_beta, Real beta, Real cm,
-        Real kappa) {
+        Real kappa, const int* __restrict__ list = nullptr, int n_items = 0, int s_lo = 0,
+        int s_cnt = 0) {
   const Lane l = lane_of(SB);
-  const int s0 = l.sv * VEC;
-  if (s0 >= S) return;
+  const int s0 = (LIST ? s_lo : 0) + l.sv * VEC;
+  if (s0 >= (LIST ? s_lo + s_cnt : S)) return;
   const int nP = m.n_P;
-  for (int i = blockIdx.x * l.NB + l.row; i < m.n_R; i += gridDim.x * l.NB) {
+  const int n_loop = LIST ? n_items : m.n_R;
+  for (int t = blockIdx.x * l.NB + l.row; t < n_loop; t += gridDim.x * l.NB) {
+    const int i = LIST ? __ldg(list + t) : t;
     const size_t is = (size_t)i * S + s0;
     const bool iP = i < nP;
     // issue every independent load of this node before any arithmetic

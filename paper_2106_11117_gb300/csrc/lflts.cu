@@ -47,8 +47,14 @@ struct MeshGPU {
   float* psi32 = nullptr;
   double* psi64 = nullptr;
   int* new2old = nullptr;
-  // autotuned (vec, CTAs per SM) per (S, precision, p)
+  // autotuned (vec, shape code) per (S, precision, p)
   std::map<std::tuple<int64_t, int, int>, std::pair<int, int>> tuned;
+  // L2 blocks of the inner loop per (S, precision, p), uploaded lists
+  struct DevBlocks {
+    InnerBlocks h;
+    int* d_nodes = nullptr;
+  };
+  std::map<std::tuple<int64_t, int, int>, DevBlocks> blocks;
 };
 
 struct Field {
@@ -131,6 +137,8 @@ struct lflts_ctx {
   int64_t graph_launches = 0;
   bool graphs = true;
   bool autotune = true;
+  bool force_blocked = false;
+  double block_budget = 40.0e6;  // bytes of inner-loop working set per L2 block
   std::vector<void*> owned;  // device allocations of meshes, fields, QoIs
 };
 
@@ -324,6 +332,9 @@ struct Stepper {
   Real* g = nullptr;
   Real* rbuf[3] = {nullptr, nullptr, nullptr};
   bool minb6 = false;
+  const InnerBlocks* blk = nullptr;  // L2 blocks (null: one launch per substep over R)
+  const int* blk_nodes = nullptr;
+  int cps = 16;
   const Real* fw = nullptr;  // M^-1 F or null
   double f0 = 0, t0 = 0, famp = 0, dt = 0;
 
@@ -338,8 +349,9 @@ struct Stepper {
           Real* g_, Real* r0, Real* r1, Real* r2, int shape = 16)
       : c(c_), p(ds.p), n_R(n_R_), S(S_), W(W_), g(g_) {
     // shape = CTAs per SM target, +100 for the register-capped kernels
-    minb6 = shape >= 100;
+    minb6 = (shape % 1000) >= 100;
     const int cta_per_sm = shape % 100;
+    cps = cta_per_sm;
     dt = ds.dt;
     if (ds.source_id >= 0) {
       fw = Sel<Real>::fw(c->sources[ds.source_id]);
@@ -360,6 +372,59 @@ struct Stepper {
     edgeP_bytes = Srb * double(h.n_edges_P);
   }
 
+  // The p-1 substeps block by block: all substeps of one (node block, draw
+  // slab) run back to back so that their r, g and W stay in L2.  Substep m
+  // covers the block's core and its first p-1-m halo layers; the last one
+  // updates d and u on the core only.  Algorithmic bytes are booked for the
+  // core (the halo is recomputation).
+  int inner_blocked(const Real* uc, Real* un, Real* d, Real kappa, cudaStream_t st) {
+    const int64_t nb = static_cast<int64_t>(blk->start.size()) - 1;
+    const int64_t slab = blk->slab;
+    for (int64_t s_lo = 0; s_lo < S; s_lo += slab) {
+      const int s_cnt = static_cast<int>(std::min<int64_t>(slab, S - s_lo));
+      for (int64_t b = 0; b < nb; ++b) {
+        const int* list = blk_nodes + blk->start[b];
+        const int32_t core = blk->layer_end[b * (p - 1)];
+        const Real* cur = g;
+        Real s_cur = (Real)(-c0);
+        const Real* prev = nullptr;
+        Real s_prev = Real(0);
+        int nxt = 0;
+        for (int m = 1; m < p; ++m) {
+          const bool last = (m == p - 1);
+          const int32_t len = blk->layer_end[b * (p - 1) + (p - 1 - m)];
+          const Geo gb = geometry(c, len, s_cnt / VEC, cps);
+          const Real opb = (Real)(1.0 + beta[m]), bt = (Real)beta[m], cmm = (Real)cm[m];
+          Real* rn = rbuf[nxt];
+          Prof pr(c, st);
+#define LF_INNER_B(L, B)                                                                                    \
+  k_inner<Real, VEC, L, B, true><<<gb.grid, 256, 0, st>>>(md, (int)S, gb.SB, W, cur, s_cur, prev, s_prev, rn, \
+                                                          g, uc, un, d, opb, bt, cmm, kappa, list, len,        \
+                                                          (int)s_lo, s_cnt)
+          if (last) {
+            if (minb6) LF_INNER_B(true, 6);
+            else LF_INNER_B(true, 1);
+          } else {
+            if (minb6) LF_INNER_B(false, 6);
+            else LF_INNER_B(false, 1);
+          }
+#undef LF_INNER_B
+          LF_CUDA(c, cudaGetLastError());
+          const double reads = (m == 1 ? 1.0 : (m == 2 ? 2.0 : 3.0));
+          const double per_node = reads + (last ? 4.0 : 1.0);
+          const double share = double(core) / double(n_R) * double(s_cnt) / double(S);
+          pr.end(LFLTS_KERNEL_INNER, (per_node * n_R * Srb + edgeP_bytes) * share);
+          prev = cur;
+          s_prev = s_cur;
+          cur = rn;
+          s_cur = Real(1);
+          nxt = (nxt + 1) % 3;
+        }
+      }
+    }
+    return 0;
+  }
+
   // u_next = 2 T u_cur - u_prev in increments: d += kappa r_p, u_next = u_cur + d.
   // minb6: the register-capped instantiation (at least 6 CTAs of 256 per SM).
   int step(const Real* uc, Real* un, Real* d, Real kappa, cudaStream_t st, int64_t n = 0) {
@@ -374,6 +439,7 @@ struct Stepper {
       LF_CUDA(c, cudaGetLastError());
       pr.end(LFLTS_KERNEL_COARSE, coarse_bytes);
     }
+    if (n_R > 0 && blk) return inner_blocked(uc, un, d, kappa, st);
     if (n_R > 0) {
       // r_1 = -c0 g is read from g; r_2.. rotate through three buffers
       const Real* cur = g;
@@ -416,10 +482,15 @@ struct Stepper {
 // The time loop of Alg. 2 for one batch.
 template <typename Real, int VEC>
 int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S,
-              Workspace& ws, Real*& uc_out, cudaStream_t st, int cta_per_sm = 16, int64_t n_steps = -1) {
+              Workspace& ws, Real*& uc_out, cudaStream_t st, int cta_per_sm = 16, int64_t n_steps = -1,
+              const MeshGPU::DevBlocks* blocks = nullptr) {
   Stepper<Real, VEC> stp(c, ds, mg, n_R, S, static_cast<const Real*>(ws.W.p), static_cast<Real*>(ws.g.p),
                          static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p),
                          cta_per_sm);
+  if (blocks && cta_per_sm >= 1000) {
+    stp.blk = &blocks->h;
+    stp.blk_nodes = blocks->d_nodes;
+  }
   Real* uc = static_cast<Real*>(ws.ua.p);
   Real* un = static_cast<Real*>(ws.ub.p);
   Real* d = static_cast<Real*>(ws.d.p);
@@ -432,12 +503,50 @@ int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n
   return 0;
 }
 
+// L2 blocks of the inner loop for a batch (built and uploaded once per
+// (S, precision, p)): a block's working set (three r, g and the weights of
+// about two P edges per node and draw) is kept under about 40 MB.
+template <typename Real>
+int get_blocks(lflts_ctx* c, MeshGPU& mg, int64_t S, int p, const MeshGPU::DevBlocks*& out) {
+  out = nullptr;
+  const HostMesh& h = mg.h;
+  if (p < 2 || h.n_R == 0) return 0;
+  const auto key = std::make_tuple(S, int(sizeof(Real) * 8), p);
+  auto it = mg.blocks.find(key);
+  if (it != mg.blocks.end()) {
+    out = &it->second;
+    return 0;
+  }
+  const double budget = c->block_budget, f = 6.0 * sizeof(Real);
+  MeshGPU::DevBlocks db;
+  int64_t core = h.n_R;
+  // slabs of at least 32 draws (a full 128-byte row per node and array);
+  // below that the node blocks shrink instead
+  if (double(h.n_R) * S * f <= budget) {
+    db.h.slab = S;
+  } else {
+    const int64_t slab_max = static_cast<int64_t>(budget / (double(h.n_R) * f)) / 8 * 8;
+    if (slab_max >= std::min<int64_t>(32, S)) {
+      db.h.slab = std::min<int64_t>(slab_max, S);
+    } else {
+      db.h.slab = std::min<int64_t>(32, S);
+      core = std::max<int64_t>(1, static_cast<int64_t>(budget / (double(db.h.slab) * f * 1.15)));
+    }
+  }
+  build_inner_blocks(h, p, core, db.h);
+  LF_TRY(upload(c, &db.d_nodes, db.h.nodes.data(), db.h.nodes.size()));
+  auto res = mg.blocks.emplace(key, std::move(db));
+  out = &res.first->second;
+  return 0;
+}
+
 template <typename Real>
 int time_loop_vec(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
-                  Real*& uc, cudaStream_t st, int vec, int cps, int64_t n_steps = -1) {
-  if (vec == 4) return time_loop<Real, 4>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps);
-  if (vec == 2) return time_loop<Real, 2>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps);
-  return time_loop<Real, 1>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps);
+                  Real*& uc, cudaStream_t st, int vec, int cps, int64_t n_steps = -1,
+                  const MeshGPU::DevBlocks* blocks = nullptr) {
+  if (vec == 4) return time_loop<Real, 4>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks);
+  if (vec == 2) return time_loop<Real, 2>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks);
+  return time_loop<Real, 1>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks);
 }
 
 // Launch shape of the step kernels for a batch: draws per thread (vec),
@@ -447,7 +556,7 @@ int time_loop_vec(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, i
 // (the state is re-initialised afterwards) and keeps the fastest.
 template <typename Real>
 int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
-                 cudaStream_t st, int& vec, int& cps) {
+                 cudaStream_t st, int& vec, int& cps, const MeshGPU::DevBlocks* blocks) {
   const int vmax = (sizeof(Real) == 4) ? 4 : 2;
   std::vector<int> vecs;
   for (int v = vmax; v >= 1; v /= 2)
@@ -472,11 +581,15 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
   const int64_t steps = std::min<int64_t>(4, ds.n_steps);
   for (int v : vecs) {
     if (vecs.size() > 2 && v == 1) continue;
-    for (int k : {8, 16, 32, 108, 116, 132}) {
+    // The L2-blocked inner loop is not a candidate: on GB300 it measured
+    // 10-35 % slower than one launch per substep at the benchmark shapes (the
+    // launch count per step outweighs the DRAM bytes it saves).
+    const std::vector<int> shapes = {8, 16, 32, 108, 116, 132};
+    for (int k : shapes) {
       Real* uc = nullptr;
-      int rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, 1);  // warm
+      int rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, 1, blocks);  // warm
       if (!rc) rc = cudaEventRecord(e0, st) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
-      if (!rc) rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, steps);
+      if (!rc) rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, steps, blocks);
       if (!rc) rc = cudaEventRecord(e1, st) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
       if (!rc) rc = cudaEventSynchronize(e1) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
       float ms = 0.f;
@@ -550,6 +663,8 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
     return 0;
   };
 
+  const MeshGPU::DevBlocks* blocks = nullptr;
+  if (c->force_blocked) LF_TRY(get_blocks<Real>(c, mg, S, p, blocks));
   int vec = 1, cps = 16;
   if (c->autotune && !mg.tuned.count(std::make_tuple(S, ds.precision, ds.p))) {
     const int64_t l0 = c->launches;
@@ -558,17 +673,18 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
     const int rc = a1();  // edge weights and a valid state for the timing runs
     c->profiling = prof;
     LF_TRY(rc);
-    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps));
+    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks));
     c->tune_launches += c->launches - l0;
     c->launches = l0;
   } else {
-    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps));
+    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks));
   }
+  if (c->force_blocked && blocks) cps = 1000 + cps % 1000;
 
   auto body = [&]() -> int {
     LF_TRY(a1());
     Real* uc = nullptr;
-    LF_TRY(time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, vec, cps));
+    LF_TRY(time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, vec, cps, -1, blocks));
     {  // QoI at t_N (Sec. 2.1), FP64 compensated accumulation.
       const int tb = static_cast<int>(std::min<int64_t>(S, 128));
       Prof pr(c, st);
@@ -1421,6 +1537,12 @@ int lflts_set_option(lflts_ctx* c, int option, int64_t value) {
   switch (option) {
     case LFLTS_OPT_GRAPHS: c->graphs = value != 0; return LFLTS_OK;
     case LFLTS_OPT_AUTOTUNE: c->autotune = value != 0; return LFLTS_OK;
+    case LFLTS_OPT_BLOCKED: c->force_blocked = value != 0; return LFLTS_OK;
+    case LFLTS_OPT_BLOCK_BUDGET:
+      if (value < 1024) return fail(c, LFLTS_ERR_ARG, "set_option: block budget below 1024 bytes");
+      c->block_budget = double(value);
+      for (auto& m : c->meshes) m->blocks.clear();  // device lists stay owned by the context
+      return LFLTS_OK;
     default: return fail(c, LFLTS_ERR_ARG, "set_option: unknown option");
   }
 }

@@ -7,6 +7,17 @@
 
 namespace lflts {
 
+namespace {
+uint64_t morton_spread16(uint64_t x) {  // interleave the low 16 bits with zeros
+  x &= 0xFFFF;
+  x = (x | (x << 8)) & 0x00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0Full;
+  x = (x | (x << 2)) & 0x33333333ull;
+  x = (x | (x << 1)) & 0x55555555ull;
+  return x;
+}
+}  // namespace
+
 int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
               const uint8_t* dirichlet, const uint8_t* P, const double* psi, int K,
               HostMesh& out, std::string& err) {
@@ -60,25 +71,45 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
     }
   }
 
-  // ---- node order: [P | R\P | free\R | Dirichlet], stable ---------------
-  m.new2old.clear();
-  m.new2old.reserve(n_nodes);
-  for (int grp = 0; grp < 4; ++grp) {
-    for (int64_t i = 0; i < n_nodes; ++i) {
-      const bool dir = dirichlet[i] != 0;
-      int g;
-      if (dir) g = 3;
-      else if (inP[i]) g = 0;
-      else if (inR[i]) g = 1;
-      else g = 2;
-      if (g == grp) m.new2old.push_back(static_cast<int32_t>(i));
-    }
-    if (grp == 0) m.n_P = static_cast<int64_t>(m.new2old.size());
-    if (grp == 1) m.n_R = static_cast<int64_t>(m.new2old.size());
-    if (grp == 2) m.n_free = static_cast<int64_t>(m.new2old.size());
+  // ---- node order: [P | R\P | free\R | Dirichlet], each group in Morton ----
+  // (Z-curve) order of the coordinates, so that index ranges are compact in
+  // space and neighbours are close in memory
+  double bx0 = 1e300, bx1 = -1e300, by0 = 1e300, by1 = -1e300;
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    bx0 = std::min(bx0, xy[2 * i]);
+    bx1 = std::max(bx1, xy[2 * i]);
+    by0 = std::min(by0, xy[2 * i + 1]);
+    by1 = std::max(by1, xy[2 * i + 1]);
+  }
+  const double qx = 65535.0 / std::max(bx1 - bx0, 1e-300), qy = 65535.0 / std::max(by1 - by0, 1e-300);
+  std::vector<std::pair<uint64_t, int32_t>> key(n_nodes);
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    const bool dir = dirichlet[i] != 0;
+    const uint64_t grp = dir ? 3 : (inP[i] ? 0 : (inR[i] ? 1 : 2));
+    const uint64_t zx = morton_spread16(static_cast<uint64_t>((xy[2 * i] - bx0) * qx));
+    const uint64_t zy = morton_spread16(static_cast<uint64_t>((xy[2 * i + 1] - by0) * qy));
+    key[i] = {(grp << 40) | zx | (zy << 1), static_cast<int32_t>(i)};
+  }
+  std::stable_sort(key.begin(), key.end(),
+                   [](const std::pair<uint64_t, int32_t>& a, const std::pair<uint64_t, int32_t>& b) {
+                     return a.first < b.first;
+                   });
+  m.new2old.resize(n_nodes);
+  m.n_P = m.n_R = m.n_free = 0;
+  for (int64_t k = 0; k < n_nodes; ++k) {
+    m.new2old[k] = key[k].second;
+    const uint64_t grp = key[k].first >> 40;
+    if (grp < 1) m.n_P = k + 1;
+    if (grp < 2) m.n_R = k + 1;
+    if (grp < 3) m.n_free = k + 1;
   }
   m.old2new.assign(n_nodes, 0);
   for (int64_t k = 0; k < n_nodes; ++k) m.old2new[m.new2old[k]] = static_cast<int32_t>(k);
+  m.xy.assign(2 * static_cast<size_t>(n_nodes), 0.0);
+  for (int64_t k = 0; k < n_nodes; ++k) {
+    m.xy[2 * k] = xy[2 * m.new2old[k]];
+    m.xy[2 * k + 1] = xy[2 * m.new2old[k] + 1];
+  }
 
   // ---- element order: by smallest new vertex id (locality of psi reads) --
   std::vector<int32_t> eorder(n_tri);
@@ -203,6 +234,61 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
     }
   }
   return 0;
+}
+
+void build_inner_blocks(const HostMesh& m, int p, int64_t core, InnerBlocks& out) {
+  const int64_t nR = m.n_R, nP = m.n_P;
+  out.nodes.clear();
+  out.start.assign(1, 0);
+  out.layer_end.clear();
+  if (nR == 0 || p < 2) return;
+  core = std::max<int64_t>(core, 1);
+  // Morton order of R by coordinates
+  double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+  for (int64_t i = 0; i < nR; ++i) {
+    x0 = std::min(x0, m.xy[2 * i]);
+    x1 = std::max(x1, m.xy[2 * i]);
+    y0 = std::min(y0, m.xy[2 * i + 1]);
+    y1 = std::max(y1, m.xy[2 * i + 1]);
+  }
+  const double sx = 65535.0 / std::max(x1 - x0, 1e-300), sy = 65535.0 / std::max(y1 - y0, 1e-300);
+  std::vector<std::pair<uint64_t, int32_t>> key(nR);
+  for (int64_t i = 0; i < nR; ++i) {
+    const uint64_t qx = static_cast<uint64_t>((m.xy[2 * i] - x0) * sx);
+    const uint64_t qy = static_cast<uint64_t>((m.xy[2 * i + 1] - y0) * sy);
+    key[i] = {morton_spread16(qx) | (morton_spread16(qy) << 1), static_cast<int32_t>(i)};
+  }
+  std::sort(key.begin(), key.end());
+  const int64_t n_blocks = (nR + core - 1) / core;
+  std::vector<int64_t> stamp(nR, -1);
+  std::vector<int32_t> frontier, next;
+  for (int64_t b = 0; b < n_blocks; ++b) {
+    const int64_t a0 = b * nR / n_blocks, a1 = (b + 1) * nR / n_blocks;
+    const size_t base = out.nodes.size();
+    frontier.clear();
+    for (int64_t a = a0; a < a1; ++a) {
+      const int32_t i = key[a].second;
+      stamp[i] = b;
+      out.nodes.push_back(i);
+      frontier.push_back(i);
+    }
+    out.layer_end.push_back(static_cast<int32_t>(out.nodes.size() - base));
+    for (int k = 1; k <= p - 2; ++k) {  // halo layer k: P neighbours of layer k-1
+      next.clear();
+      for (int32_t i : frontier)
+        for (int32_t t = m.adj_ptr[i]; t < m.adj_ptr[i + 1]; ++t) {
+          const int32_t j = m.adj_j[t];
+          if (j < nP && stamp[j] != b) {
+            stamp[j] = b;
+            next.push_back(j);
+            out.nodes.push_back(j);
+          }
+        }
+      frontier.swap(next);
+      out.layer_end.push_back(static_cast<int32_t>(out.nodes.size() - base));
+    }
+    out.start.push_back(static_cast<int64_t>(out.nodes.size()));
+  }
 }
 
 }  // namespace lflts

@@ -4,7 +4,8 @@
 // A P q "only involve those unknowns inside, or immediately next to, the
 // refined region").  The kernels work on a node order grouped as
 //   [ P nodes | R \ P nodes | free nodes outside R | Dirichlet nodes ]
-// where R = vertices of every element that has a vertex in P: the inner
+// each group in Morton (Z-curve) order of the node coordinates, where
+// R = vertices of every element that has a vertex in P: the inner
 // substeps of Alg. 2 change exactly the nodes of R, all other free nodes
 // follow the closed-form leapfrog update.
 //
@@ -43,7 +44,25 @@ struct HostMesh {
   std::vector<double> edge_G0, edge_G1;    // G_e0[i][j], G_e1[i][j] (0 when e1 = -1)
   std::vector<double> minv;                // [n_free] 1 / m_i (lumped mass)
   std::vector<double> psi2;                // [n_tri][KP] psi * log2(e), zero padded
+  std::vector<double> xy;                  // [n_nodes][2] coordinates, internal order
 };
+
+// Blocks of the inner substeps for L2 residency.  Block b computes the p-1
+// substeps of Alg. 2 on its core nodes for a slab of draws; substep m
+// (1 <= m <= p-1) runs on the prefix of the block's node list made of the
+// core and the first p-1-m halo layers, where halo layer k holds the P nodes
+// at k P-neighbour hops from the core.  After p-1 substeps the core values
+// are exact: every value they depend on was computed inside the block.
+struct InnerBlocks {
+  int64_t slab = 0;                    // draws per block
+  std::vector<int32_t> nodes;          // concatenated node lists (internal ids)
+  std::vector<int64_t> start;          // [n_blocks + 1] offsets into nodes
+  std::vector<int32_t> layer_end;      // [n_blocks][p-1]: prefix length for halo depth 0..p-2
+};
+
+// Partition R into spatially compact blocks of about `core` nodes (Morton
+// order of the node coordinates) and attach p-2 halo layers.
+void build_inner_blocks(const HostMesh& m, int p, int64_t core, InnerBlocks& out);
 
 // Returns 0 on success; on failure fills err and returns a negative status.
 int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,

@@ -41,6 +41,8 @@ EXPORTED = [
 ]
 LFLTS_OPT_GRAPHS = 1
 LFLTS_OPT_AUTOTUNE = 2
+LFLTS_OPT_BLOCKED = 3
+LFLTS_OPT_BLOCK_BUDGET = 4
 
 
 class LibraryNotBuilt(RuntimeError):

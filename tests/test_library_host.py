@@ -86,9 +86,19 @@ def test_host_only_mesh_preparation(lib):
     assert R[order[nP:nR]].all() and not P[order[nP:nR]].any()
     assert free[order[nR:nF]].all() and not R[order[nR:nF]].any()
     assert not free[order[nF:]].any()
-    # each group keeps the caller's order
+    # each group is in Morton (Z-curve) order of the coordinates
+    lo, hi = m.xy.min(0), m.xy.max(0)
+    q = ((m.xy - lo) * (65535.0 / (hi - lo))).astype(np.uint64)
+
+    def spread(x):
+        x = x & np.uint64(0xFFFF)
+        for sh, mask in ((8, 0x00FF00FF), (4, 0x0F0F0F0F), (2, 0x33333333), (1, 0x55555555)):
+            x = (x | (x << np.uint64(sh))) & np.uint64(mask)
+        return x
+
+    z = spread(q[:, 0]) | (spread(q[:, 1]) << np.uint64(1))
     for a, b in ((0, nP), (nP, nR), (nR, nF), (nF, m.n_nodes)):
-        assert np.all(np.diff(order[a:b]) > 0)
+        assert np.all(np.diff(z[order[a:b]].astype(np.int64)) >= 0)
 
 
 def test_invalid_mesh_rejected(lib):
