@@ -1,0 +1,101 @@
+"""Parity at the benchmark's full sizes, in its launch configuration (needs a
+GB300; about two minutes).
+
+square128-p8-K8-L5: the level pairs go through lflts_run_pairs exactly as in
+bench.py (mesh 0 solves 8192 + 2048 draws in one batch).  Levels 0 and 1 are
+checked draw by draw against the FP64 oracle (FP32 tolerance 1e-5 of the
+batch's QoI scale).  On levels 2-4 the oracle needs hours per draw; there the
+checks are properties that hold at any size: a draw's QoI is the same bit for
+bit whether it is solved inside the full batch or alone; the solve is linear
+in u0 (doubling u0 doubles every QoI); and the FP32 path agrees with the FP64
+path to 1e-5 of the QoI scale.
+
+Doubling is exact operation by operation except where values underflow: the
+far tail of the Gaussian u0 and the values just ahead of the discrete wave
+front fall below the FP32 normal range, where rounding is not invariant under
+scaling.  The two trajectories then take different rounding decisions, and
+the difference settles at the FP32 rounding level of the QoI (about 3e-8 of
+its scale at levels 1-2), so the FP32 check allows 1e-6.  The FP64 path
+stays far from its underflow threshold over these horizons and is checked to
+1e-14."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_11117_gb300 import build, lflts
+    build.build()
+    ctx = lflts.Context(0)
+    yield lflts, ctx
+    ctx.close()
+
+
+def _pair_jobs(lf, hs, xis, prec):
+    jobs, outs = [], []
+    for l, x in enumerate(xis):
+        dQ, Qf, sums = np.zeros(x.shape[0]), np.zeros(x.shape[0]), np.zeros(4)
+        j = lf.PairJob()
+        j.fine = hs[l].desc(prec)
+        if l > 0:
+            j.coarse = hs[l - 1].desc(prec)
+            j.has_coarse = 1
+        j.xi, j.S = x.ctypes.data, x.shape[0]
+        j.dQ, j.Qf, j.sums = dQ.ctypes.data, Qf.ctypes.data, sums.ctypes.data
+        jobs.append(j)
+        outs.append((dQ, Qf, sums))
+    return jobs, outs
+
+
+def test_levels_0_1_sampled_against_oracle(env):
+    from oracle.lts import solve_qoi
+    from workload import CONFIG_BATCHED as cfg, level_problem, xi_uniform
+    lf, ctx = env
+    levs = [level_problem(cfg, l) for l in (0, 1)]
+    hs = [ctx.add_level(l) for l in levs]
+    xis = [xi_uniform(cfg.seed, l, cfg.samples[l], cfg.K) for l in (0, 1)]
+    jobs, outs = _pair_jobs(lf, hs, xis, 32)
+    lf.lflts_run_pairs(ctx.h, jobs)
+    scale0 = np.abs(outs[0][1]).max()
+    for i in (0, 4097, cfg.samples[0] - 1):
+        q = solve_qoi(levs[0], xis[0][i])
+        assert abs(outs[0][1][i] - q) <= 1e-5 * scale0
+        assert outs[0][0][i] == outs[0][1][i]
+    scale1 = np.abs(outs[1][1]).max()
+    i = 1234
+    qf, qc = solve_qoi(levs[1], xis[1][i]), solve_qoi(levs[0], xis[1][i])
+    assert abs(outs[1][1][i] - qf) <= 1e-5 * scale1
+    assert abs(outs[1][0][i] - (qf - qc)) <= 2e-5 * scale1
+
+
+@pytest.mark.parametrize("level", [2, 3, 4])
+def test_large_levels_properties(env, level):
+    from workload import CONFIG_BATCHED as cfg, level_problem, xi_uniform
+    lf, ctx = env
+    lev = level_problem(cfg, level)
+    h = ctx.add_level(lev)
+    S = cfg.samples[level] + (cfg.samples[level + 1] if level + 1 < cfg.levels else 0)
+    parts = [xi_uniform(cfg.seed, level, cfg.samples[level], cfg.K)]
+    if level + 1 < cfg.levels:
+        parts.append(xi_uniform(cfg.seed, level + 1, cfg.samples[level + 1], cfg.K))
+    xi = np.ascontiguousarray(np.concatenate(parts))
+    assert xi.shape[0] == S
+    Q = ctx.solve(h, xi, precision=32)                    # the benchmark's batch
+    assert np.isfinite(Q).all() and np.abs(Q).max() > 0
+    pick = np.array(sorted({0, 1, S // 2, S - 1}))
+    sub = np.ascontiguousarray(xi[pick])
+    np.testing.assert_array_equal(ctx.solve(h, sub, precision=32), Q[pick])
+    # linearity in u0
+    h2 = ctx.add_level(dict(lev, u0=2.0 * lev["u0"]))
+    np.testing.assert_allclose(ctx.solve(h2, sub, precision=32), 2.0 * Q[pick], rtol=0,
+                               atol=1e-6 * np.abs(Q).max())
+    if level <= 3:
+        Q64 = ctx.solve(h, sub[:2], precision=64)
+        assert np.abs(Q64 - Q[pick][:2]).max() <= 1e-5 * np.abs(Q).max()
+        np.testing.assert_allclose(ctx.solve(h2, sub[:2], precision=64), 2.0 * Q64, rtol=0,
+                                   atol=1e-14 * np.abs(Q64).max())
