@@ -392,9 +392,10 @@ def time_to_eps(eps=2e-3):
 
 # DRAM traffic per launch = algorithmic bytes x (dram__bytes_read.sum +
 # dram__bytes_write.sum) / algorithmic bytes of one ncu capture of the same
-# kernel on a smaller batch (traffic grows in proportion to the draws):
-# profiles/k_inner_square128-L3-S32.md (k_inner unchanged since the capture).
-TRAFFIC_RATIO = {"inner": 657.9 / 619.0}
+# kernel on a smaller batch (traffic grows in proportion to the draws): the
+# capture of k_inner on level 3 of the square128-p8-K8 hierarchy with 32 draws,
+# Morton node order, 643.7 MB of DRAM traffic for 619.0 MB algorithmic.
+TRAFFIC_RATIO = {"inner": 643.7 / 619.0}
 
 
 def run_reference(args):
