@@ -271,8 +271,6 @@ def run_ours(args):
     barrier()
     clocks = Clocks(local)
     clocks.start()
-    lf.lflts_profile_reset(ctx.h)
-    lf.lflts_profile_enable(ctx.h, True)
     n0 = lf.lflts_launch_count(ctx.h)
     torch.cuda.synchronize()
     barrier()
@@ -285,9 +283,7 @@ def run_ours(args):
     barrier()
     ms = e0.elapsed_time(e1)
     launches = lf.lflts_launch_count(ctx.h) - n0
-    lf.lflts_profile_enable(ctx.h, False)
     clk = clocks.stop()
-    prof = {k: lf.lflts_profile_read(ctx.h, k) for k in ("init", "coarse", "inner", "qoi", "sums")}
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -311,6 +307,15 @@ def run_ours(args):
             el = float(t.item())
         e2e = {"value": W["units"] * world * args.steps / el, "unit": UNIT,
                "h2d_bytes_per_step": W["h2d"] * world, "d2h_bytes_per_step": W["d2h"] * world}
+
+    # one more step with per-launch CUDA events (each group's kernels timed on
+    # its own stream, groups queued whole) for the kernel split and roofline
+    lf.lflts_profile_reset(ctx.h)
+    lf.lflts_profile_enable(ctx.h, True)
+    step()
+    torch.cuda.synchronize()
+    lf.lflts_profile_enable(ctx.h, False)
+    prof = {k: lf.lflts_profile_read(ctx.h, k) for k in ("init", "coarse", "inner", "qoi", "sums")}
 
     # roofline of the dominant kernel class
     peak, peak_kind = _peaks()
@@ -342,7 +347,10 @@ def run_ours(args):
                            "solves_per_step": {f"mesh{l}": S for l, S in sorted(W["solves"].items())},
                            "units_per_step": W["units"] * world,
                            "l2": "inputs larger than L2 (per-mesh state >= 1 GB), no flush",
-                           "parallelism": f"samples sharded, dp{world}"},
+                           "parallelism": f"samples sharded, dp{world}",
+                           "timing": "timed steps without per-launch events (solves replayed as CUDA "
+                                     "graphs on concurrent streams); roofline and kernel_classes from one "
+                                     "further step with CUDA events around every launch"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "time_to_eps": tte,
                 "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
@@ -396,6 +404,181 @@ def time_to_eps(eps=2e-3):
 # capture of k_inner on level 3 of the square128-p8-K8 hierarchy with 32 draws,
 # Morton node order, 643.7 MB of DRAM traffic for 619.0 MB algorithmic.
 TRAFFIC_RATIO = {"inner": 643.7 / 619.0}
+
+
+def _timed_passes(lf, ctx, step, st, warmup, steps, profile_steps=1, local=0):
+    """W warm-up steps, K timed steps (CUDA events on `st`, no per-launch
+    events, so graphs run where the solves fit one), then `profile_steps`
+    steps with per-launch events for the kernel-class split."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    n0 = lf.lflts_launch_count(ctx.h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = lf.lflts_launch_count(ctx.h) - n0
+    clk = clocks.stop()
+    if profile_steps < 1:
+        return ms, launches, clk, None
+    lf.lflts_profile_reset(ctx.h)
+    lf.lflts_profile_enable(ctx.h, True)
+    for _ in range(profile_steps):
+        step()
+    torch.cuda.synchronize()
+    lf.lflts_profile_enable(ctx.h, False)
+    prof = {k: lf.lflts_profile_read(ctx.h, k) for k in lf.KERNEL_CLASSES}
+    return ms, launches, clk, prof
+
+
+def _roofline(prof, classes, names, traffic_ratio=None):
+    peak, peak_kind = _peaks()
+    total = sum(v["ms"] for v in prof.values()) or 1.0
+    dom = max(classes, key=lambda k: prof[k]["ms"])
+    pd = prof[dom]
+    achieved = pd["alg_bytes"] / (pd["ms"] * 1e-3) / 1e9 if pd["ms"] > 0 else 0.0
+    per = pd["alg_bytes"] / max(pd["launches"], 1)
+    return {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": traffic_ratio * per if traffic_ratio else None, "alg_bytes_per_launch": per,
+            "launches": pd["launches"], "avg_launch_ms": pd["ms"] / max(pd["launches"], 1),
+            "share_of_kernel_time": round(pd["ms"] / total, 4)}
+
+
+def _classes_json(prof):
+    return {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                "alg_GBps": round(v["alg_bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
+            for k, v in prof.items() if v["launches"]}
+
+
+def run_lshape(args):
+    """Uneven batching on the graded L-shape (lshape-graded-s2-K16-ricker):
+    4 levels (m = 58..464 layers, p = 3, 5, 9, 17), Gaussian draws with their
+    own time steps bucketed by (fine, coarse) step counts, Ricker source; all
+    buckets of all level pairs in one lflts_run_pairs call (merged per mesh
+    and step count, concurrent streams, autotuned shapes incl. the fused
+    inner kernel).  FP32 state, FP64 QoI and sums."""
+    import numpy as np
+    import torch
+    from paper_2106_11117_gb300 import build, lflts
+    from workload import CONFIG_LSHAPE as cfg, lshape_level, lshape_steps, xi_gaussian
+    build.build()
+    torch.cuda.set_device(0)
+    ctx = lflts.Context(0)
+    levs = [lshape_level(cfg, l) for l in range(cfg.levels)]
+    hs = [ctx.add_level(dict(lv, dt=lv["T"], n_steps=1)) for lv in levs]
+
+    def w(h):
+        return h.info["n_free"] + h.p * h.info["n_R"]
+
+    jobs, keep, units, buckets, h2d = [], [], 0, 0, 0
+    for l in range(cfg.levels):
+        xi = xi_gaussian(cfg.seed, l, cfg.samples[l], cfg.K, cfg.sigma)
+        nf = lshape_steps(levs[l], xi)
+        nc = lshape_steps(levs[l - 1], xi) if l else np.zeros_like(nf)
+        for kf, kc in sorted(set(zip(nf.tolist(), nc.tolist()))):
+            sel = np.nonzero((nf == kf) & (nc == kc))[0]
+            x = torch.from_numpy(np.ascontiguousarray(xi[sel])).cuda()
+            o = [torch.zeros(len(sel), dtype=torch.float64, device="cuda") for _ in range(2)]
+            o.append(torch.zeros(4, dtype=torch.float64, device="cuda"))
+            j = lflts.PairJob()
+            j.fine = hs[l].desc(cfg.precision)
+            j.fine.dt, j.fine.n_steps = cfg.T / kf, kf
+            if l:
+                j.coarse = hs[l - 1].desc(cfg.precision)
+                j.coarse.dt, j.coarse.n_steps = cfg.T / kc, kc
+                j.has_coarse = 1
+            j.xi, j.S = x.data_ptr(), len(sel)
+            j.dQ, j.Qf, j.sums = o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr()
+            jobs.append(j)
+            keep.append((x, o))
+            units += len(sel) * (kf * w(hs[l]) + (kc * w(hs[l - 1]) if l else 0))
+            buckets += 1
+            h2d += x.numel() * 8
+    st = torch.cuda.current_stream()
+
+    def step():
+        lflts.lflts_run_pairs(ctx.h, jobs, lflts.LFLTS_MEM_DEVICE, st.cuda_stream)
+
+    ms, launches, clk, prof = _timed_passes(lflts, ctx, step, st, args.warmup, args.steps)
+    value = units * args.steps / (ms * 1e-3)
+    names = {"coarse": "k_coarse", "inner": "k_inner / k_inner_fused"}
+    line = {"mode": "lshape", "metric": UNIT + " (uneven batching, graded L-shape)", "value": value,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{cfg.name}: L-shape [-1,1]^2 minus [0,1]x[-1,0], graded s={cfg.s}, "
+                                   f"m={cfg.m0}*2^l layers, p=2q+1 with q={cfg.q_levels}, K={cfg.K}, "
+                                   f"xi~N(0,{cfg.sigma}^2), Ricker f0={cfg.f0} at {cfg.source_xy}, "
+                                   f"samples {'/'.join(map(str, cfg.samples))}, per-draw steps bucketed",
+                       "buckets": buckets, "units_per_step": units,
+                       "mesh_nodes": [h.info["n_nodes"] for h in hs], "n_R": [h.info["n_R"] for h in hs],
+                       "l2": "largest meshes' state above L2, no flush"},
+            "roofline": _roofline(prof, ("coarse", "inner"), names), "gpu_launches": launches,
+            "clocks": clk, "stats": lflts.lflts_get_stats(ctx.h), "kernel_classes": _classes_json(prof),
+            "h2d_bytes_per_step": h2d}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args):
+    """dQ/dxi of every draw on square256-p8-K16 (256^2 base cells, box refined
+    8x, 16 field terms, 1024 draws, 2000 outer steps of the CFL step, so
+    T = 2000 dt): forward with checkpoints every 64 steps, segment
+    recomputation, the adjoint recursion and the contraction with dK/dxi;
+    FP32 and FP64.  Throughput counts the forward work units of the solve
+    (S N (n_free + p |R|)) per gradient evaluation."""
+    import torch
+    from paper_2106_11117_gb300 import build, lflts
+    from workload import CONFIG_ADJOINT as cfg, level_problem, xi_uniform
+    build.build()
+    torch.cuda.set_device(0)
+    N, ckpt = 2000, 64
+    lev = level_problem(cfg, 0)
+    lev = dict(lev, n_steps=N, T=N * lev["dt"])
+    ctx = lflts.Context(0)
+    h = ctx.add_level(lev)
+    S = cfg.samples[0]
+    xi = torch.from_numpy(xi_uniform(cfg.seed, 0, S, cfg.K)).cuda()
+    units = S * N * (h.info["n_free"] + cfg.p * h.info["n_R"])
+    st = torch.cuda.current_stream()
+    out = {"mode": "adjoint", "metric": UNIT + " of dQ/dxi (forward + adjoint)", "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "data": "synthetic",
+           "config": {"workload": f"{cfg.name}: unit square, {cfg.n0}^2 base cells, box {cfg.box} refined "
+                                  f"p={cfg.p}, K={cfg.K}, xi~U(-1,1), S={S}, N={N} outer steps "
+                                  f"(dt={lev['dt']:.4e}, T={lev['T']:.4f}), checkpoints every {ckpt}",
+                      "n_free": h.info["n_free"], "n_R": h.info["n_R"], "n_edges": h.info["n_edges"],
+                      "units_per_gradient": units}}
+    names = {"coarse": "k_coarse", "inner": "k_inner", "adj_inner": "k_adj_inner (+ recomputed r)",
+             "adj_edges": "k_adj_edges", "grad": "k_grad_contract"}
+    for prec in (32, 64):
+        Q = torch.zeros(S, dtype=torch.float64, device="cuda")
+        G = torch.zeros(S, cfg.K, dtype=torch.float64, device="cuda")
+        d = h.desc(prec)
+
+        def step():
+            lflts.lflts_grad_xi(ctx.h, d, xi, S, ckpt, Q, G, lflts.LFLTS_MEM_DEVICE, st.cuda_stream)
+
+        # the FP64 gradient takes minutes: timed only, no extra profiled pass
+        ms, launches, clk, prof = _timed_passes(lflts, ctx, step, st, args.warmup, args.steps,
+                                                profile_steps=1 if prec == 32 else 0)
+        out[f"fp{prec}"] = {"value": units * args.steps / (ms * 1e-3), "ms_per_gradient": ms / args.steps,
+                            "gpu_launches": launches, "clocks": clk,
+                            "roofline": _roofline(prof, tuple(names), names) if prof else None,
+                            "kernel_classes": _classes_json(prof) if prof else None,
+                            "grad_finite": bool(torch.isfinite(G).all().item()),
+                            "grad_abs_max": float(G.abs().max().item())}
+    out["value"] = out["fp32"]["value"]
+    out["dtype"] = "f32"
+    ctx.close()
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args):
@@ -531,7 +714,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["batched", "plain", "bandwidth"], default="batched")
+    ap.add_argument("--config", choices=["batched", "plain", "bandwidth", "lshape", "adjoint"],
+                    default="batched")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cores", type=int, default=0)
@@ -550,6 +734,10 @@ def main():
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.config == "lshape":
+        run_lshape(args)
+    elif args.config == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -63,7 +63,11 @@ enum {
   LFLTS_KERNEL_INNER = 2,  /* one inner LTS substep on R (Alg. 2 loop)      */
   LFLTS_KERNEL_QOI = 3,    /* QoI reduction (both stages)                   */
   LFLTS_KERNEL_SUMS = 4,   /* MLMC level sums                               */
-  LFLTS_KERNEL_CLASSES = 5
+  LFLTS_KERNEL_ADJ_INNER = 5, /* lflts_grad_xi: recomputed a(u_n) and r_2..r_{p-1} on R and the
+                                 adjoint inner recursion rho_{p-1}..rho_1                 */
+  LFLTS_KERNEL_ADJ_EDGES = 6, /* lflts_grad_xi: per-edge FP64 accumulation of the gradient    */
+  LFLTS_KERNEL_GRAD = 7,      /* lflts_grad_xi: adjoint seed and the contraction with dK/dxi */
+  LFLTS_KERNEL_CLASSES = 8
 };
 
 /* Options for lflts_set_option. */
@@ -77,7 +81,11 @@ enum {
                              nodes, draw slabs, all substeps of a block back to back; same results
                              bit for bit, fewer DRAM bytes, more launches); 0 (default): one launch
                              per substep over R */
-  LFLTS_OPT_BLOCK_BUDGET = 4 /* bytes of inner-loop working set per L2 block (default 40e6) */
+  LFLTS_OPT_BLOCK_BUDGET = 4, /* bytes of inner-loop working set per L2 block (default 40e6) */
+  LFLTS_OPT_FUSED_INNER = 5   /* all p-1 inner substeps of a step in one launch, R and the draws of a
+                                 CTA in shared memory (only where 4 |R| x slab values fit in 200 KB;
+                                 same results bit for bit): 0 never, 1 (default) when the autotuner
+                                 measures it faster, 2 always where it fits */
 };
 
 /* Library version (major*10000 + minor*100 + patch). */

@@ -133,6 +133,96 @@ k_adj_edges(int64_t n_edges, int n_P, int n_R, int S, int SB, const int2* __rest
   }
 }
 
+// FP32 path of the edge accumulation: VEC draws per thread, FP32 arithmetic
+// (the state it reads is FP32), added into a per-segment FP32 accumulator
+// Aseg that k_adj_fold adds into the FP64 A at the end of every checkpoint
+// segment (so FP32 sums run over at most one segment of steps).  Same terms
+// as k_adj_edges.  FP64 work on this GPU runs at a small fraction of the
+// FP32 rate, which made the FP64 form of this kernel ALU-bound.
+struct AdjConsts32 {
+  float c[65];
+  float gk;  // gamma * kappa
+  float kappa;
+  int p;
+};
+
+template <int VEC>
+__global__ void __launch_bounds__(256)
+k_adj_edges32(int64_t n_edges, int n_P, int n_R, int S, int SB, const int2* __restrict__ ends,
+              const float* __restrict__ u, const float* __restrict__ nu, const float* __restrict__ gs,
+              const float* __restrict__ rs, const float* __restrict__ rho, float* __restrict__ Aseg,
+              const AdjConsts32 k) {
+  const Lane l = lane_of(SB);
+  const int s0 = l.sv * VEC;
+  if (s0 >= S) return;
+  const size_t RS = (size_t)n_R * S;
+  for (int64_t e = (int64_t)blockIdx.x * l.NB + l.row; e < n_edges; e += (int64_t)gridDim.x * l.NB) {
+    const int2 ij = ends[e];
+    const int i = ij.x, j = ij.y;  // i < j
+    const size_t oi = (size_t)i * S + s0, oj = (size_t)j * S + s0;
+    const Pack<float, VEC> ui = ldp<float, VEC>(u + oi), uj = ldp<float, VEC>(u + oj);
+    const size_t oa = (size_t)e * S + s0;
+    Pack<float, VEC> a = ldp<float, VEC>(Aseg + oa);
+    float du[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) du[q] = ui.v[q] - uj.v[q];
+    if (i >= n_P) {  // no P endpoint: leapfrog adjoint term
+      const Pack<float, VEC> vi = ldp<float, VEC>(nu + oi), vj = ldp<float, VEC>(nu + oj);
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) a.v[q] += k.gk * (vi.v[q] - vj.v[q]) * du[q];
+    } else {
+      // i in P; j in R, or a Dirichlet node (values 0)
+      const bool jR = j < n_R, jP = j < n_P;
+      auto rho_of = [&](int mm, size_t o) -> Pack<float, VEC> {  // rho_mm at offset o, mm = 1..p
+        if (mm == k.p) {
+          Pack<float, VEC> r = ldp<float, VEC>(nu + o);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) r.v[q] *= k.kappa;
+          return r;
+        }
+        return ldp<float, VEC>(rho + (size_t)(mm - 1) * RS + o);
+      };
+      auto pr_of = [&](int mm, size_t o) -> Pack<float, VEC> {  // (P r_mm) at offset o, mm = 1..p-1
+        if (mm == 1) {
+          Pack<float, VEC> r = ldp<float, VEC>(gs + o);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) r.v[q] *= -k.c[0];
+          return r;
+        }
+        return ldp<float, VEC>(rs + (size_t)(mm - 2) * RS + o);
+      };
+      Pack<float, VEC> zero;
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) zero.v[q] = 0.f;
+      Pack<float, VEC> ri = rho_of(1, oi), rj = jR ? rho_of(1, oj) : zero;
+      float acc[VEC];
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) acc[q] = k.c[0] * (ri.v[q] - rj.v[q]) * du[q];
+      for (int mm = 1; mm < k.p; ++mm) {
+        const Pack<float, VEC> pi = pr_of(mm, oi), pj = jP ? pr_of(mm, oj) : zero;
+        ri = rho_of(mm + 1, oi);
+        rj = jR ? rho_of(mm + 1, oj) : zero;
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+          const float dy = du[q] + pi.v[q] - pj.v[q];
+          acc[q] += k.c[mm] * (ri.v[q] - rj.v[q]) * dy;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) a.v[q] += acc[q];
+    }
+    stp<float, VEC>(Aseg + oa, a);
+  }
+}
+
+// A += Aseg, Aseg = 0 (end of a checkpoint segment of the FP32 adjoint).
+__global__ void k_adj_fold(int64_t n, float* __restrict__ Aseg, double* __restrict__ A) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    A[t] += (double)Aseg[t];
+    Aseg[t] = 0.f;
+  }
+}
+
 // nu_N = M^{-1} g_Q on the QoI nodes (the state arrays are zeroed before).
 template <typename Real>
 __global__ void k_adj_seed(int nnz, int S, const int* __restrict__ idx, const double* __restrict__ gq,

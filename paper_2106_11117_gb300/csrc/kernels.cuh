@@ -96,6 +96,36 @@ __device__ __forceinline__ void stp(Real* __restrict__ p, const Pack<Real, V>& r
   }
 }
 
+// Store of the first nvalid of V values (nvalid >= V: one vector store).
+template <typename Real, int V>
+__device__ __forceinline__ void stp_lim(Real* __restrict__ p, const Pack<Real, V>& r, int nvalid) {
+  if (nvalid >= V) {
+    stp<Real, V>(p, r);
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+      if (k < nvalid) p[k] = r.v[k];
+  }
+}
+
+// Ragged batches (draws with their own time step dt_s and step count): the
+// step constants belong to a reference step dt_ref and every draw's edge
+// weights carry (dt_s / dt_ref)^2, since c_0, c_m and gamma are dt^2 times
+// constants of p and nu.  The forcing r(t_n) M^-1 F then needs the same
+// factor and the draw's own time t_n = n dt_s; it is evaluated here, on the
+// few nodes that carry a load.  dts == nullptr: a uniform batch.
+struct RaggedF {
+  const double* dts;
+  double dt_ref, f0, t0, amp;
+  int n;
+};
+__device__ __forceinline__ double ricker_scaled(const RaggedF& rf, int s) {
+  const double dt = rf.dts[s];
+  const double t = double(rf.n) * dt, x = M_PI * M_PI * rf.f0 * rf.f0 * (t - rf.t0) * (t - rf.t0);
+  const double sc = (dt / rf.dt_ref) * (dt / rf.dt_ref);
+  return rf.amp * (1.0 - 2.0 * x) * exp(-x) * sc;
+}
+
 __device__ __forceinline__ float exp2_r(float x) { return exp2f(x); }
 __device__ __forceinline__ double exp2_r(double x) { return exp2(x); }
 
@@ -121,7 +151,7 @@ template <typename Real, int KP>
 __global__ void __launch_bounds__(256)
 k_edge_weights(int64_t n_edges, int S, int SB, const int2* __restrict__ ee,
                const Real* __restrict__ eg, const Real* __restrict__ psi2,
-               const Real* __restrict__ xi, Real* __restrict__ W) {
+               const Real* __restrict__ xi, Real* __restrict__ W, const Real* __restrict__ sig = nullptr) {
   const int ls = threadIdx.x & (SB - 1);
   const int NB = blockDim.x / SB;
   const int s = blockIdx.y * SB + ls;
@@ -129,6 +159,7 @@ k_edge_weights(int64_t n_edges, int S, int SB, const int2* __restrict__ ee,
   Real xr[KP];
 #pragma unroll
   for (int k = 0; k < KP; ++k) xr[k] = xi[(size_t)s * KP + k];
+  const Real sg = sig ? sig[s] : Real(1);  // ragged batch: (dt_s / dt_ref)^2
   for (int64_t e = (int64_t)blockIdx.x * NB + threadIdx.x / SB; e < n_edges; e += (int64_t)gridDim.x * NB) {
     const int2 el = ee[e];
     Real w = Real(0);
@@ -142,7 +173,7 @@ k_edge_weights(int64_t n_edges, int S, int SB, const int2* __restrict__ ee,
       for (int k = 0; k < KP; ++k) acc = fma(xr[k], __ldg(pe + k), acc);
       w = fma(exp2_r(acc), eg[2 * e + side], w);
     }
-    W[(size_t)e * S + s] = w;
+    W[(size_t)e * S + s] = sig ? w * sg : w;
   }
 }
 
@@ -151,14 +182,18 @@ k_edge_weights(int64_t n_edges, int S, int SB, const int2* __restrict__ ee,
 //   outside R: d += -kappa*gamma*g, u_next = u_n + d
 //   inside  R: store g
 // ---------------------------------------------------------------------------
-template <typename Real, int VEC, int MINB = 1>
+// RAG: a ragged batch (draws [S_lim, S) finished: their u and d are not
+// written; per-draw forcing amplitude); otherwise S_lim and rf are unused.
+template <typename Real, int VEC, int MINB = 1, bool RAG = false>
 __global__ void __launch_bounds__(256, MINB)
 k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real* __restrict__ u,
          Real* __restrict__ u_next, Real* __restrict__ d, Real* __restrict__ g, Real kappa_gamma,
-         const Real* __restrict__ fw, Real famp) {
+         const Real* __restrict__ fw, Real famp, int S_lim, RaggedF rf) {
   const Lane l = lane_of(SB);
   const int s0 = l.sv * VEC;
-  if (s0 >= S) return;
+  const int lim = RAG ? S_lim : S;
+  if (s0 >= lim) return;
+  const int nvalid = lim - s0;
   for (int i = blockIdx.x * l.NB + l.row; i < m.n_free; i += gridDim.x * l.NB) {
     const size_t is = (size_t)i * S + s0;
     const bool outside = i >= m.n_R;
@@ -194,10 +229,18 @@ k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real*
       for (int k = 0; k < VEC; ++k) acc[k] = fma(wo.v[k], uo.v[k] - ui.v[k], acc[k]);
     }
     // g = a(u_n) - M^-1 F(t_n): fw = M^-1 F (sample independent), famp = r(t_n)
-    const Real fi = fw ? famp * fw[i] : Real(0);
     Pack<Real, VEC> gi;
+    if constexpr (RAG) {
+      const Real f = fw ? fw[i] : Real(0);
+      const bool own = rf.dts && f != Real(0);  // the draw's own t_n and dt^2 factor
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) gi.v[k] = mi * acc[k] - fi;
+      for (int k = 0; k < VEC; ++k)
+        gi.v[k] = mi * acc[k] - (own ? (Real)ricker_scaled(rf, s0 + k) * f : famp * f);
+    } else {
+      const Real fi = fw ? famp * fw[i] : Real(0);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) gi.v[k] = mi * acc[k] - fi;
+    }
     if (outside) {
       Pack<Real, VEC> un;
 #pragma unroll
@@ -205,8 +248,13 @@ k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real*
         dn.v[k] = dn.v[k] - kappa_gamma * gi.v[k];
         un.v[k] = ui.v[k] + dn.v[k];
       }
-      stp<Real, VEC>(d + is, dn);
-      stp<Real, VEC>(u_next + is, un);
+      if constexpr (RAG) {
+        stp_lim<Real, VEC>(d + is, dn, nvalid);
+        stp_lim<Real, VEC>(u_next + is, un, nvalid);
+      } else {
+        stp<Real, VEC>(d + is, dn);
+        stp<Real, VEC>(u_next + is, un);
+      }
     } else {
       stp<Real, VEC>(g + is, gi);
     }
@@ -222,17 +270,19 @@ k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real*
 // LIST: the launch covers the nodes list[0..n_items) (an L2 block of the
 // inner loop) and the draws [s_lo, s_lo + s_cnt); otherwise all of R and all
 // draws.  The arithmetic per node and draw is the same either way.
-template <typename Real, int VEC, bool LAST, int MINB = 1, bool LIST = false>
+template <typename Real, int VEC, bool LAST, int MINB = 1, bool LIST = false, bool RAG = false>
 __global__ void __launch_bounds__(256, MINB)
 k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
         const Real* __restrict__ cur, Real s_cur, const Real* __restrict__ prev, Real s_prev,
         Real* __restrict__ r_next, const Real* __restrict__ g, const Real* __restrict__ u,
         Real* __restrict__ u_next, Real* __restrict__ d, Real one_plus_beta, Real beta, Real cm,
-        Real kappa, const int* __restrict__ list = nullptr, int n_items = 0, int s_lo = 0,
+        Real kappa, int S_lim, const int* __restrict__ list = nullptr, int n_items = 0, int s_lo = 0,
         int s_cnt = 0) {
   const Lane l = lane_of(SB);
   const int s0 = (LIST ? s_lo : 0) + l.sv * VEC;
-  if (s0 >= (LIST ? s_lo + s_cnt : S)) return;
+  const int lim = RAG ? S_lim : S;
+  if (s0 >= (LIST ? s_lo + s_cnt : lim)) return;
+  const int nvalid = lim - s0;
   const int nP = m.n_P;
   const int n_loop = LIST ? n_items : m.n_R;
   for (int t = blockIdx.x * l.NB + l.row; t < n_loop; t += gridDim.x * l.NB) {
@@ -306,11 +356,155 @@ k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
         dn.v[k] = dn.v[k] + kappa * rn.v[k];
         un.v[k] = ui.v[k] + dn.v[k];
       }
-      stp<Real, VEC>(d + is, dn);
-      stp<Real, VEC>(u_next + is, un);
+      if constexpr (RAG) {
+        stp_lim<Real, VEC>(d + is, dn, nvalid);
+        stp_lim<Real, VEC>(u_next + is, un, nvalid);
+      } else {
+        stp<Real, VEC>(d + is, dn);
+        stp<Real, VEC>(u_next + is, un);
+      }
     } else {
       stp<Real, VEC>(r_next + is, rn);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// All p-1 inner substeps of one outer step in one launch, for a small R.
+//
+// CTA b owns the draws [b SL, b SL + SL) (SL = SBf VEC) of every R node.
+// g and the recursion r_m of those draws live in shared memory, plane 0 = g
+// (r_1 = -c_0 g is never formed), planes 1..3 = r_2, r_3, ... in rotation,
+// and __syncthreads separates the substeps: the draws of different CTAs
+// never interact, so no grid-wide synchronisation is needed.  Per node the
+// arithmetic is that of k_inner, term by term and in the same order, so the
+// result is the same bit for bit; only the global traffic differs (g, u, d on
+// R and the P-edge weights once per step instead of once per substep).
+// Shared memory: 4 n_R SL sizeof(Real) bytes.
+template <typename Real>
+struct InnerCoef {
+  Real opb[64], beta[64], cm[64];  // (1 + beta_m), beta_m, c_m for m = 1..p-1
+  Real neg_c0;                     // -c_0 (the scale of r_1 = -c_0 g)
+  int p;
+};
+
+template <typename Real, int VEC, bool RAG = false>
+__global__ void __launch_bounds__(256)
+k_inner_fused(MeshDev<Real> m, int S, int SBf, const Real* __restrict__ W, const Real* __restrict__ g,
+              const Real* __restrict__ u, Real* __restrict__ u_next, Real* __restrict__ d,
+              const InnerCoef<Real> k, Real kappa, int S_lim) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  const int SL = SBf * VEC;
+  const int nR = m.n_R, nP = m.n_P;
+  const size_t plane = (size_t)nR * SL;
+  const int lane = threadIdx.x % SBf, row = threadIdx.x / SBf, NB = blockDim.x / SBf;
+  const int s0 = blockIdx.x * SL + lane * VEC;  // first draw of this thread (VEC divides S)
+  const int lim = RAG ? S_lim : S;
+  const bool active = s0 < lim;
+  const int nvalid = lim - s0;
+  const int o = lane * VEC;
+  if (active)
+    for (int i = row; i < nR; i += NB)
+      stp<Real, VEC>(sm + (size_t)i * SL + o, ldp<Real, VEC>(g + (size_t)i * S + s0));
+  __syncthreads();
+  const Real* cur = sm;
+  Real s_cur = k.neg_c0;
+  const Real* prev = nullptr;
+  Real s_prev = Real(0);
+  int nxt = 1;
+  for (int mm = 1; mm < k.p; ++mm) {
+    const bool last = (mm == k.p - 1);
+    Real* r_next = sm + nxt * plane;
+    const Real one_plus_beta = k.opb[mm], beta = k.beta[mm], cm = k.cm[mm];
+    if (active) {
+      for (int i = row; i < nR; i += NB) {
+        const size_t io = (size_t)i * SL + o;
+        const bool iP = i < nP;
+        const Nb4 nb = load_nb4(m, i);
+        const int t0 = m.adj_ptr[i] + 4, t1 = m.adj_ptr[i + 1];
+        const Pack<Real, VEC> rc = ldp<Real, VEC>(cur + io);
+        const Pack<Real, VEC> gi = ldp<Real, VEC>(sm + io);
+        Pack<Real, VEC> rj[4], w[4], rp;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = nb.j[q];
+          const bool jP = j >= 0 && j < nP;
+          if (jP || (iP && j >= 0)) {
+            w[q] = ldp<Real, VEC>(W + (size_t)nb.e[q] * S + s0);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < VEC; ++kk) w[q].v[kk] = Real(0);
+          }
+          if (jP) {
+            rj[q] = ldp<Real, VEC>(cur + (size_t)j * SL + o);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < VEC; ++kk) rj[q].v[kk] = Real(0);
+          }
+        }
+        if (prev) {
+          rp = ldp<Real, VEC>(prev + io);
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < VEC; ++kk) rp.v[kk] = Real(0);
+        }
+        const Real mi = m.minv[i];
+        Real vi[VEC], acc[VEC];
+#pragma unroll
+        for (int kk = 0; kk < VEC; ++kk) {
+          vi[kk] = iP ? s_cur * rc.v[kk] : Real(0);
+          acc[kk] = Real(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int kk = 0; kk < VEC; ++kk) acc[kk] = fma(w[q].v[kk], s_cur * rj[q].v[kk] - vi[kk], acc[kk]);
+        for (int t = t0; t < t1; ++t) {  // neighbours beyond the fourth (rare)
+          const int2 on = m.adj[t];
+          const bool jP = on.x < nP;
+          if (!jP && !iP) break;  // sorted: no P neighbour left
+          const Pack<Real, VEC> wo = ldp<Real, VEC>(W + (size_t)on.y * S + s0);
+          if (jP) {
+            const Pack<Real, VEC> ro = ldp<Real, VEC>(cur + (size_t)on.x * SL + o);
+#pragma unroll
+            for (int kk = 0; kk < VEC; ++kk) acc[kk] = fma(wo.v[kk], s_cur * ro.v[kk] - vi[kk], acc[kk]);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < VEC; ++kk) acc[kk] = fma(wo.v[kk], -vi[kk], acc[kk]);
+          }
+        }
+        Pack<Real, VEC> rn;
+#pragma unroll
+        for (int kk = 0; kk < VEC; ++kk)
+          rn.v[kk] = one_plus_beta * (s_cur * rc.v[kk]) - beta * (s_prev * rp.v[kk]) - cm * (gi.v[kk] + mi * acc[kk]);
+        if (last) {
+          const size_t is = (size_t)i * S + s0;
+          const Pack<Real, VEC> ui = ldp<Real, VEC>(u + is);
+          Pack<Real, VEC> dn = ldp<Real, VEC>(d + is), un;
+#pragma unroll
+          for (int kk = 0; kk < VEC; ++kk) {
+            dn.v[kk] = dn.v[kk] + kappa * rn.v[kk];
+            un.v[kk] = ui.v[kk] + dn.v[kk];
+          }
+          if constexpr (RAG) {
+            stp_lim<Real, VEC>(d + is, dn, nvalid);
+            stp_lim<Real, VEC>(u_next + is, un, nvalid);
+          } else {
+            stp<Real, VEC>(d + is, dn);
+            stp<Real, VEC>(u_next + is, un);
+          }
+        } else {
+          stp<Real, VEC>(r_next + io, rn);
+        }
+      }
+    }
+    __syncthreads();
+    prev = cur;
+    s_prev = s_cur;
+    cur = r_next;
+    s_cur = Real(1);
+    nxt = nxt % 3 + 1;
   }
 }
 
@@ -320,7 +514,7 @@ k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
 template <typename Real>
 __global__ void k_init_state(int64_t n_nodes, int S, const Real* __restrict__ u0,
                              const Real* __restrict__ v0, Real dt, Real* __restrict__ ua,
-                             Real* __restrict__ ub, Real* __restrict__ d) {
+                             Real* __restrict__ ub, Real* __restrict__ d, const double* __restrict__ dts = nullptr) {
   const int64_t total = n_nodes * (int64_t)S;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
        k += (int64_t)gridDim.x * blockDim.x) {
@@ -328,7 +522,7 @@ __global__ void k_init_state(int64_t n_nodes, int S, const Real* __restrict__ u0
     const Real v = u0[i];
     ua[k] = v;
     ub[k] = v;
-    d[k] = v0 ? dt * v0[i] : Real(0);
+    d[k] = v0 ? (dts ? (Real)dts[k % S] : dt) * v0[i] : Real(0);  // d_0 = dt v0 (dt of the draw)
   }
 }
 
@@ -365,9 +559,9 @@ struct Neumaier {
 template <typename Real>
 __global__ void k_qoi_partial(const Real* __restrict__ u, int S, const int* __restrict__ idx,
                               const double* __restrict__ gw, int nnz, int chunk,
-                              double* __restrict__ ps, double* __restrict__ pc) {
-  const int s = blockIdx.y * blockDim.x + threadIdx.x;
-  if (s >= S) return;
+                              double* __restrict__ ps, double* __restrict__ pc, int s_lo, int s_hi) {
+  const int s = s_lo + blockIdx.y * blockDim.x + threadIdx.x;  // draws [s_lo, s_hi)
+  if (s >= s_hi) return;
   const int c = blockIdx.x;
   const int k0 = c * chunk, k1 = min(nnz, k0 + chunk);
   Neumaier acc;
@@ -394,12 +588,13 @@ __global__ void k_qoi_final(int n_chunks, int S, const double* __restrict__ ps,
 // Gather the state back to the caller's node order in FP64.
 template <typename Real>
 __global__ void k_gather_state(int64_t n_nodes, int S, const int* __restrict__ new2old,
-                               const Real* __restrict__ u, double* __restrict__ out) {
-  const int64_t total = n_nodes * (int64_t)S;
+                               const Real* __restrict__ u, double* __restrict__ out, int s_lo, int s_hi) {
+  const int64_t w = s_hi - s_lo;  // draws [s_lo, s_hi)
+  const int64_t total = n_nodes * w;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = k / S, s = k % S;
-    out[(int64_t)new2old[i] * S + s] = (double)u[k];
+    const int64_t i = k / w, s = s_lo + k % w;
+    out[(int64_t)new2old[i] * S + s] = (double)u[(size_t)i * S + s];
   }
 }
 

@@ -10,10 +10,12 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/lflts.h"
@@ -76,6 +78,11 @@ struct Qoi {
   double* g = nullptr;
 };
 
+// Largest solve (in kernels) captured into one CUDA graph.
+constexpr int64_t kGraphMaxKernels = 120000;
+// Outer steps queued per turn when lflts_run_pairs interleaves long solves.
+constexpr int64_t kSliceSteps = 32;
+
 // Everything a captured solve graph depends on.
 struct GraphKey {
   int mesh, qoi, u0, v0, precision, p;
@@ -84,6 +91,8 @@ struct GraphKey {
   const void *xi, *Q, *uN, *ua, *ub, *d, *g, *r0, *r1, *r2, *W, *xipad, *qps, *qpc;
   int vec, cps, source;
   double f0, t0, famp;
+  uint64_t ragged;           // segment list of a ragged batch (0: uniform)
+  const void *dts, *sig;
   bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
@@ -95,12 +104,15 @@ struct GraphEntry {
 
 struct Workspace {
   Buf ua, ub, d, g, r0, r1, r2, W, xipad, xraw, qps, qpc, Q, uN;
+  Buf dts, sig;                        // per-draw dt and (dt / dt_ref)^2 of a ragged batch
+  std::vector<double> h_dts;           // host copies of the two (kept for the async copies)
+  std::vector<unsigned char> h_sig;
   std::vector<GraphEntry> graphs;
 };
 
 // Buffers of the adjoint (gradient) solve.
 struct GradBufs {
-  Buf ckpt, segU, rs, rho, gs, A, nua, nub, dnu, part, xraw, Q, G;
+  Buf ckpt, segU, rs, rho, gs, A, Aseg, nua, nub, dnu, part, xraw, Q, G;
 };
 
 struct ProfRec {
@@ -139,6 +151,7 @@ struct lflts_ctx {
   bool autotune = true;
   bool force_blocked = false;
   double block_budget = 40.0e6;  // bytes of inner-loop working set per L2 block
+  int fused_mode = 1;            // fused inner kernel: 0 never, 1 autotuned, 2 always where it fits
   std::vector<void*> owned;  // device allocations of meshes, fields, QoIs
 };
 
@@ -202,6 +215,8 @@ cudaEvent_t get_event(lflts_ctx* c) {
   return e;
 }
 
+void harvest(lflts_ctx* c);
+
 struct Prof {
   lflts_ctx* c;
   cudaStream_t st;
@@ -218,9 +233,35 @@ struct Prof {
       cudaEvent_t b = get_event(c);
       cudaEventRecord(b, st);
       c->pending.push_back({cls, a, b, bytes});
+      if (c->pending.size() >= 16384) harvest(c);
     }
   }
 };
+
+// Books the profiled launches whose end event has completed and recycles
+// their events, without waiting: long profiled runs keep a bounded list.
+void harvest(lflts_ctx* c) {
+  size_t keep = 0;
+  for (size_t k = 0; k < c->pending.size(); ++k) {
+    ProfRec& r = c->pending[k];
+    if (cudaEventQuery(r.b) == cudaSuccess) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        c->prof_ms[r.cls] += ms;
+        c->prof_bytes[r.cls] += r.bytes;
+        c->prof_launches[r.cls] += 1;
+      }
+      c->pool.push_back(r.a);
+      c->pool.push_back(r.b);
+    } else {
+      c->pending[keep++] = r;
+    }
+  }
+  c->pending.resize(keep);
+  // a query of an event still in flight answers "not ready": not an error of
+  // any launch (each launch's own status was taken right after it)
+  if (cudaPeekAtLastError() == cudaErrorNotReady) (void)cudaGetLastError();
+}
 
 // Chebyshev constants of the stabilised scheme (Sec. 3.3) and the derived
 // increment-form coefficients.  out: delta, omega, c0, gamma, then for
@@ -313,11 +354,26 @@ struct Sel<double> {
 
 // Geometry of the node/edge kernels: SB lanes of VEC samples per node.
 Geo geometry_vec(const lflts_ctx* c, int64_t n, int64_t S, int vec, int cta_per_sm = 16) {
-  return geometry(c, n, S / vec, cta_per_sm);
+  return geometry(c, n, (S + vec - 1) / vec, cta_per_sm);  // a ragged prefix may end inside a vector
+}
+
+// Plan of the fused inner kernel (all substeps of a step in one launch, R in
+// shared memory): lanes per node SBf (draw slab SL = SBf vec) and dynamic
+// shared memory; smem = 0 when R does not fit.  The slab widens while R is
+// small against the CTA and the batch still gives two CTAs per SM.
+constexpr size_t kFusedSmemMax = 200 * 1024;
+inline void fused_plan(const lflts_ctx* c, int n_R, int64_t S, int vec, size_t rb, int& SBf, size_t& smem) {
+  SBf = 1;
+  smem = 0;
+  if (n_R < 1) return;
+  while (SBf < 8 && int64_t(n_R) * SBf * 2 <= 256 && (S / (int64_t(SBf) * 2 * vec)) >= 2 * c->sms) SBf *= 2;
+  const size_t need = 4 * size_t(n_R) * size_t(SBf) * size_t(vec) * rb;
+  if (need <= kFusedSmemMax) smem = need;
 }
 
 // One step of Alg. 2 for one batch (see kernels.cuh for the u-form): the
-// coarse launch over the free nodes, then p-1 inner launches over R.
+// coarse launch over the free nodes, then p-1 inner launches over R (or one
+// fused launch for a small R).
 template <typename Real, int VEC>
 struct Stepper {
   lflts_ctx* c = nullptr;
@@ -335,8 +391,16 @@ struct Stepper {
   const InnerBlocks* blk = nullptr;  // L2 blocks (null: one launch per substep over R)
   const int* blk_nodes = nullptr;
   int cps = 16;
+  bool fused = false;  // all inner substeps in one launch (R in shared memory)
+  int fSB = 1;
+  size_t fsmem = 0;
+  int fgrid = 1;
+  InnerCoef<Real> coef{};
   const Real* fw = nullptr;  // M^-1 F or null
   double f0 = 0, t0 = 0, famp = 0, dt = 0;
+  int64_t S_act = 0;         // draws [0, S_act) still stepping (ragged batches)
+  const double* dts = nullptr;  // per-draw time steps of a ragged batch (device), or null
+  const MeshGPU* mgp = nullptr;
 
   // r(t) of the Ricker wavelet times the amplitude
   Real source_amp(double t) const {
@@ -347,8 +411,9 @@ struct Stepper {
 
   Stepper(lflts_ctx* c_, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R_, int64_t S_, const Real* W_,
           Real* g_, Real* r0, Real* r1, Real* r2, int shape = 16)
-      : c(c_), p(ds.p), n_R(n_R_), S(S_), W(W_), g(g_) {
-    // shape = CTAs per SM target, +100 for the register-capped kernels
+      : c(c_), p(ds.p), n_R(n_R_), S(S_), W(W_), g(g_), S_act(S_), mgp(&mg) {
+    // shape = CTAs per SM target, +100 for the register-capped kernels,
+    // +2000 for the fused inner kernel
     minb6 = (shape % 1000) >= 100;
     const int cta_per_sm = shape % 100;
     cps = cta_per_sm;
@@ -370,6 +435,48 @@ struct Stepper {
     Srb = double(S) * sizeof(Real);
     coarse_bytes = Srb * (4.0 * h.n_free - 2.0 * n_R + double(h.n_edges));
     edgeP_bytes = Srb * double(h.n_edges_P);
+    if (shape >= 2000 && n_R > 0 && p > 1 && p <= 64) {
+      fused_plan(c, n_R, S, VEC, sizeof(Real), fSB, fsmem);
+      fused = fsmem > 0;
+      const int64_t SL = int64_t(fSB) * VEC;
+      fgrid = static_cast<int>((S + SL - 1) / SL);
+      coef.p = p;
+      coef.neg_c0 = (Real)(-c0);
+      for (int m = 1; m < p; ++m) {
+        coef.opb[m] = (Real)(1.0 + beta[m]);
+        coef.beta[m] = (Real)beta[m];
+        coef.cm[m] = (Real)cm[m];
+      }
+    }
+  }
+
+  // Narrow the launches to the draws [0, S_new) (a ragged batch whose other
+  // draws have reached their own step count).
+  void set_active(int64_t S_new) {
+    S_act = S_new;
+    const HostMesh& h = mgp->h;
+    gc = geometry_vec(c, h.n_free, S_act, VEC, cps);
+    gi = geometry_vec(c, std::max(n_R, 1), S_act, VEC, cps);
+    Srb = double(S_act) * sizeof(Real);
+    coarse_bytes = Srb * (4.0 * h.n_free - 2.0 * n_R + double(h.n_edges));
+    edgeP_bytes = Srb * double(h.n_edges_P);
+    if (fused) {
+      const int64_t SL = int64_t(fSB) * VEC;
+      fgrid = static_cast<int>((S_act + SL - 1) / SL);
+    }
+  }
+
+  RaggedF ragged(int64_t n) const {
+    RaggedF rf{};
+    if (dts && fw) {
+      rf.dts = dts;
+      rf.dt_ref = dt;
+      rf.f0 = f0;
+      rf.t0 = t0;
+      rf.amp = famp;
+      rf.n = static_cast<int>(n);
+    }
+    return rf;
   }
 
   // The p-1 substeps block by block: all substeps of one (node block, draw
@@ -399,8 +506,8 @@ struct Stepper {
           Prof pr(c, st);
 #define LF_INNER_B(L, B)                                                                                    \
   k_inner<Real, VEC, L, B, true><<<gb.grid, 256, 0, st>>>(md, (int)S, gb.SB, W, cur, s_cur, prev, s_prev, rn, \
-                                                          g, uc, un, d, opb, bt, cmm, kappa, list, len,        \
-                                                          (int)s_lo, s_cnt)
+                                                          g, uc, un, d, opb, bt, cmm, kappa, (int)S, list,     \
+                                                          len, (int)s_lo, s_cnt)
           if (last) {
             if (minb6) LF_INNER_B(true, 6);
             else LF_INNER_B(true, 1);
@@ -432,14 +539,34 @@ struct Stepper {
       Prof pr(c, st);
       const Real kg = (Real)(double(kappa) * gamma);
       const Real fa = source_amp(double(n) * dt);
-      if (minb6)
-        k_coarse<Real, VEC, 6><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg, fw, fa);
-      else
-        k_coarse<Real, VEC, 1><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg, fw, fa);
+      const RaggedF rf = ragged(n);
+#define LF_COARSE(B, RG) \
+  k_coarse<Real, VEC, B, RG><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg, fw, fa, (int)S_act, rf)
+      if (dts) {  // ragged batch
+        if (minb6) LF_COARSE(6, true);
+        else LF_COARSE(1, true);
+      } else {
+        if (minb6) LF_COARSE(6, false);
+        else LF_COARSE(1, false);
+      }
+#undef LF_COARSE
       LF_CUDA(c, cudaGetLastError());
       pr.end(LFLTS_KERNEL_COARSE, coarse_bytes);
     }
     if (n_R > 0 && blk) return inner_blocked(uc, un, d, kappa, st);
+    if (n_R > 0 && fused) {
+      Prof pr(c, st);
+      if (dts)
+        k_inner_fused<Real, VEC, true><<<fgrid, 256, fsmem, st>>>(md, (int)S, fSB, W, g, uc, un, d, coef, kappa,
+                                                                  (int)S_act);
+      else
+        k_inner_fused<Real, VEC, false><<<fgrid, 256, fsmem, st>>>(md, (int)S, fSB, W, g, uc, un, d, coef, kappa,
+                                                                   (int)S_act);
+      LF_CUDA(c, cudaGetLastError());
+      // g, u and d in, d and u out on R, the P-edge weights: once per step
+      pr.end(LFLTS_KERNEL_INNER, 5.0 * n_R * Srb + edgeP_bytes);
+      return 0;
+    }
     if (n_R > 0) {
       // r_1 = -c0 g is read from g; r_2.. rotate through three buffers
       const Real* cur = g;
@@ -452,15 +579,18 @@ struct Stepper {
         const Real opb = (Real)(1.0 + beta[m]), bt = (Real)beta[m], cmm = (Real)cm[m];
         Real* rn = rbuf[nxt];
         Prof pr(c, st);
-#define LF_INNER(L, B)                                                                                    \
-  k_inner<Real, VEC, L, B><<<gi.grid, 256, 0, st>>>(md, (int)S, gi.SB, W, cur, s_cur, prev, s_prev, rn, g, \
-                                                    uc, un, d, opb, bt, cmm, kappa)
-        if (last) {
-          if (minb6) LF_INNER(true, 6);
-          else LF_INNER(true, 1);
+#define LF_INNER(L, B, RG)                                                                                     \
+  k_inner<Real, VEC, L, B, false, RG><<<gi.grid, 256, 0, st>>>(md, (int)S, gi.SB, W, cur, s_cur, prev, s_prev, rn, \
+                                                               g, uc, un, d, opb, bt, cmm, kappa, (int)S_act)
+        if (dts) {  // ragged batch: only the last substep writes u and d
+          if (last) LF_INNER(true, 1, true);
+          else LF_INNER(false, 1, false);
+        } else if (last) {
+          if (minb6) LF_INNER(true, 6, false);
+          else LF_INNER(true, 1, false);
         } else {
-          if (minb6) LF_INNER(false, 6);
-          else LF_INNER(false, 1);
+          if (minb6) LF_INNER(false, 6, false);
+          else LF_INNER(false, 1, false);
         }
 #undef LF_INNER
         LF_CUDA(c, cudaGetLastError());
@@ -487,7 +617,7 @@ int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n
   Stepper<Real, VEC> stp(c, ds, mg, n_R, S, static_cast<const Real*>(ws.W.p), static_cast<Real*>(ws.g.p),
                          static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p),
                          cta_per_sm);
-  if (blocks && cta_per_sm >= 1000) {
+  if (blocks && cta_per_sm >= 1000 && cta_per_sm < 2000) {
     stp.blk = &blocks->h;
     stp.blk_nodes = blocks->d_nodes;
   }
@@ -549,6 +679,137 @@ int time_loop_vec(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, i
   return time_loop<Real, 1>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks);
 }
 
+// Whether the fused inner kernel can run this batch; raises its dynamic
+// shared-memory limit once it can (outside any graph capture).
+template <typename Real>
+bool fused_ok(lflts_ctx* c, int n_R, int64_t S, int vec, int p) {
+  if (n_R < 1 || p < 2 || p > 64) return false;
+  int SBf = 1;
+  size_t smem = 0;
+  fused_plan(c, n_R, S, vec, sizeof(Real), SBf, smem);
+  if (smem == 0) return false;
+  cudaError_t e = cudaSuccess;
+  const int mx = int(kFusedSmemMax);
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (vec == 4) {
+    e = cudaFuncSetAttribute(k_inner_fused<Real, 4, false>, attr, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inner_fused<Real, 4, true>, attr, mx);
+  } else if (vec == 2) {
+    e = cudaFuncSetAttribute(k_inner_fused<Real, 2, false>, attr, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inner_fused<Real, 2, true>, attr, mx);
+  } else {
+    e = cudaFuncSetAttribute(k_inner_fused<Real, 1, false>, attr, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inner_fused<Real, 1, true>, attr, mx);
+  }
+  return e == cudaSuccess;
+}
+
+// Draw segments of a ragged batch: draws [off, off + cnt) take n_steps steps
+// of dt.  Segments are sorted by n_steps, descending, so that the draws still
+// stepping always form a prefix of the batch.  A uniform batch is one segment.
+struct RaggedSeg {
+  int64_t off, cnt, n_steps;
+  double dt;
+};
+struct RaggedSpec {
+  std::vector<RaggedSeg> segs;
+  const double* d_dts = nullptr;  // [S] time step of every draw
+  const void* d_sig = nullptr;    // [S] (dt_s / dt_ref)^2 in the batch precision
+  uint64_t hash = 0;              // of the segment list (graph key)
+};
+
+// The time loop of one batch, queued in slices of outer steps.  lflts_run_pairs
+// uses the slices to keep several long solves (too long for one graph) on
+// their streams at once: a single host thread that queued one solve's whole
+// loop would block on that stream's launch queue while the others ran dry.
+// When a segment of a ragged batch reaches its step count its QoI is taken
+// and the launches narrow to the draws still stepping.
+struct SliceTask {
+  virtual ~SliceTask() = default;
+  virtual int advance(int64_t steps) = 0;  // queue up to `steps` more outer steps
+  virtual bool done() const = 0;
+  virtual int finish() = 0;                // queue the QoI of the last segments
+};
+
+template <typename Real>
+struct LoopOut {  // what the loop does with finished draws
+  std::function<int(const Real* u, int64_t s_lo, int64_t s_hi)> qoi_range;
+  std::function<int()> qoi_final;
+};
+
+template <typename Real, int VEC>
+struct SlicedLoop : SliceTask {
+  lflts_ctx* c;
+  Stepper<Real, VEC> stp;
+  Real* uc;
+  Real* un;
+  Real* d;
+  int64_t n = 0, N;
+  cudaStream_t st;
+  std::vector<RaggedSeg> segs;
+  size_t active;  // segments 0 .. active-1 still step
+  LoopOut<Real> out;
+  SlicedLoop(lflts_ctx* c_, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
+             cudaStream_t st_, int cps, const MeshGPU::DevBlocks* blocks, const RaggedSpec* rg, LoopOut<Real> o)
+      : c(c_),
+        stp(c_, ds, mg, n_R, S, static_cast<const Real*>(ws.W.p), static_cast<Real*>(ws.g.p),
+            static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p), cps),
+        uc(static_cast<Real*>(ws.ua.p)),
+        un(static_cast<Real*>(ws.ub.p)),
+        d(static_cast<Real*>(ws.d.p)),
+        N(ds.n_steps),
+        st(st_),
+        out(std::move(o)) {
+    if (blocks && cps >= 1000 && cps < 2000) {
+      stp.blk = &blocks->h;
+      stp.blk_nodes = blocks->d_nodes;
+    }
+    if (rg) {
+      segs = rg->segs;
+      stp.dts = rg->d_dts;
+    } else {
+      segs.push_back({0, S, ds.n_steps, ds.dt});
+    }
+    active = segs.size();
+  }
+  // QoI of the segments that have taken all their steps (at step n)
+  int freeze() {
+    bool narrowed = false;
+    while (active > 0 && segs[active - 1].n_steps <= n) {
+      const RaggedSeg& sg = segs[active - 1];
+      LF_TRY(out.qoi_range(uc, sg.off, sg.off + sg.cnt));
+      --active;
+      narrowed = true;
+    }
+    if (narrowed && active > 0) stp.set_active(segs[active - 1].off + segs[active - 1].cnt);
+    return 0;
+  }
+  int advance(int64_t steps) override {
+    for (int64_t k = 0; k < steps && n < N; ++k, ++n) {
+      LF_TRY(freeze());
+      LF_TRY(stp.step(uc, un, d, (n == 0) ? Real(1) : Real(2), st, n));
+      std::swap(uc, un);
+    }
+    return 0;
+  }
+  bool done() const override { return n >= N; }
+  int finish() override {
+    LF_TRY(freeze());
+    return out.qoi_final();
+  }
+};
+
+template <typename Real>
+std::unique_ptr<SliceTask> make_sliced(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R,
+                                       int64_t S, Workspace& ws, cudaStream_t st, int vec, int cps,
+                                       const MeshGPU::DevBlocks* blocks, const RaggedSpec* rg, LoopOut<Real> o) {
+  if (vec == 4)
+    return std::make_unique<SlicedLoop<Real, 4>>(c, ds, mg, n_R, S, ws, st, cps, blocks, rg, std::move(o));
+  if (vec == 2)
+    return std::make_unique<SlicedLoop<Real, 2>>(c, ds, mg, n_R, S, ws, st, cps, blocks, rg, std::move(o));
+  return std::make_unique<SlicedLoop<Real, 1>>(c, ds, mg, n_R, S, ws, st, cps, blocks, rg, std::move(o));
+}
+
 // Launch shape of the step kernels for a batch: draws per thread (vec),
 // CTAs per SM and the register cap (shape code cps: CTAs per SM, +100 for the
 // instantiation limited to 40 registers so that 6 CTAs of 256 fit an SM).  With autotuning on, the first solve of a (mesh, S,
@@ -563,6 +824,10 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
     if (S % v == 0) vecs.push_back(v);
   vec = vecs.front();
   cps = 16;
+  if (c->fused_mode == 2 && !blocks && fused_ok<Real>(c, n_R, S, vec, ds.p)) {
+    cps = 2016;
+    return 0;
+  }
   if (!c->autotune) return 0;
   const auto key = std::make_tuple(S, ds.precision, ds.p);
   auto it = mg.tuned.find(key);
@@ -583,8 +848,11 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
     if (vecs.size() > 2 && v == 1) continue;
     // The L2-blocked inner loop is not a candidate: on GB300 it measured
     // 10-35 % slower than one launch per substep at the benchmark shapes (the
-    // launch count per step outweighs the DRAM bytes it saves).
-    const std::vector<int> shapes = {8, 16, 32, 108, 116, 132};
+    // launch count per step outweighs the DRAM bytes it saves).  The fused
+    // inner kernel is, where R fits in shared memory.
+    std::vector<int> shapes = {8, 16, 32, 108, 116, 132};
+    if (c->fused_mode >= 1 && !blocks && fused_ok<Real>(c, n_R, S, v, ds.p))
+      for (int k : {8, 16, 32, 108, 116, 132}) shapes.push_back(2000 + k);
     for (int k : shapes) {
       Real* uc = nullptr;
       int rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, 1, blocks);  // warm
@@ -619,7 +887,8 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
 template <typename Real, int KP>
 int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qoi& q,
                  const Field& u0, const Field* v0, const double* d_xi, int64_t S, double* d_Q,
-                 double* d_uN, Workspace& ws, cudaStream_t st) {
+                 double* d_uN, Workspace& ws, cudaStream_t st, std::unique_ptr<SliceTask>* defer,
+                 const RaggedSpec* rg) {
   const HostMesh& h = mg.h;
   const size_t rb = sizeof(Real);
   const int64_t n_nodes = h.n_nodes;
@@ -652,11 +921,13 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
     k_xi_pad<Real, KP><<<blocks_for(S * KP, 256, 4096), 256, 0, st>>>((int)S, h.K, d_xi, xi);
     LF_CUDA(c, cudaGetLastError());
     k_init_state<Real><<<blocks_for(n_nodes * S, 256, c->sms * 32), 256, 0, st>>>(
-        n_nodes, (int)S, Sel<Real>::field(u0), v0 ? Sel<Real>::field(*v0) : nullptr, (Real)ds.dt, ua, ub, d);
+        n_nodes, (int)S, Sel<Real>::field(u0), v0 ? Sel<Real>::field(*v0) : nullptr, (Real)ds.dt, ua, ub, d,
+        rg ? rg->d_dts : nullptr);
     LF_CUDA(c, cudaGetLastError());
     const Geo ge = geometry(c, std::max<int64_t>(h.n_edges, 1), S);
     k_edge_weights<Real, KP><<<ge.grid, 256, 0, st>>>(h.n_edges, (int)S, ge.SB, mg.ee, Sel<Real>::eg(mg),
-                                                      Sel<Real>::psi(mg), xi, W);
+                                                      Sel<Real>::psi(mg), xi, W,
+                                                      rg ? static_cast<const Real*>(rg->d_sig) : nullptr);
     LF_CUDA(c, cudaGetLastError());
     pr.end(LFLTS_KERNEL_INIT, double(S) * rb * (3.0 * n_nodes + double(h.n_edges)));
     c->launches += 2;  // three kernels in this class
@@ -664,7 +935,7 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   };
 
   const MeshGPU::DevBlocks* blocks = nullptr;
-  if (c->force_blocked) LF_TRY(get_blocks<Real>(c, mg, S, p, blocks));
+  if (c->force_blocked && !rg) LF_TRY(get_blocks<Real>(c, mg, S, p, blocks));
   int vec = 1, cps = 16;
   if (c->autotune && !mg.tuned.count(std::make_tuple(S, ds.precision, ds.p))) {
     const int64_t l0 = c->launches;
@@ -681,35 +952,60 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   }
   if (c->force_blocked && blocks) cps = 1000 + cps % 1000;
 
-  auto body = [&]() -> int {
-    LF_TRY(a1());
-    Real* uc = nullptr;
-    LF_TRY(time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, vec, cps, -1, blocks));
-    {  // QoI at t_N (Sec. 2.1), FP64 compensated accumulation.
-      const int tb = static_cast<int>(std::min<int64_t>(S, 128));
-      Prof pr(c, st);
-      k_qoi_partial<Real><<<dim3(n_chunks, static_cast<unsigned>((S + tb - 1) / tb)), tb, 0, st>>>(
-          uc, (int)S, q.idx, q.g, q.nnz, chunk, static_cast<double*>(ws.qps.p), static_cast<double*>(ws.qpc.p));
-      LF_CUDA(c, cudaGetLastError());
-      k_qoi_final<<<blocks_for(S, 128, 1 << 20), 128, 0, st>>>(n_chunks, (int)S, static_cast<double*>(ws.qps.p),
-                                                              static_cast<double*>(ws.qpc.p), d_Q, c->d_bad);
-      LF_CUDA(c, cudaGetLastError());
-      pr.end(LFLTS_KERNEL_QOI, double(q.nnz) * S * rb);
-      c->launches++;
-    }
+  // QoI at each draw's final step (Sec. 2.1; FP64 compensated sums), stage 1
+  // per finished draw range, stage 2 once; optional gather of u_N.  Captured
+  // by value: a sliced solve runs them later.
+  const Qoi* qp = &q;
+  Workspace* wsp = &ws;
+  const int* new2old = mg.new2old;
+  int* d_bad = c->d_bad;
+  LoopOut<Real> lo;
+  lo.qoi_range = [=](const Real* uc, int64_t s_lo, int64_t s_hi) -> int {
+    const int64_t w = s_hi - s_lo;
+    const int tb = static_cast<int>(std::min<int64_t>(w, 128));
+    Prof pr(c, st);
+    k_qoi_partial<Real><<<dim3(n_chunks, static_cast<unsigned>((w + tb - 1) / tb)), tb, 0, st>>>(
+        uc, (int)S, qp->idx, qp->g, qp->nnz, chunk, static_cast<double*>(wsp->qps.p),
+        static_cast<double*>(wsp->qpc.p), (int)s_lo, (int)s_hi);
+    LF_CUDA(c, cudaGetLastError());
+    pr.end(LFLTS_KERNEL_QOI, double(qp->nnz) * w * rb);
     if (d_uN) {
-      k_gather_state<Real><<<blocks_for(n_nodes * S, 256, c->sms * 32), 256, 0, st>>>(n_nodes, (int)S, mg.new2old,
-                                                                                     uc, d_uN);
+      k_gather_state<Real><<<blocks_for(n_nodes * w, 256, c->sms * 32), 256, 0, st>>>(n_nodes, (int)S, new2old,
+                                                                                     uc, d_uN, (int)s_lo,
+                                                                                     (int)s_hi);
       LF_CUDA(c, cudaGetLastError());
       c->launches++;
     }
     return 0;
   };
+  lo.qoi_final = [=]() -> int {
+    k_qoi_final<<<blocks_for(S, 128, 1 << 20), 128, 0, st>>>(n_chunks, (int)S, static_cast<double*>(wsp->qps.p),
+                                                            static_cast<double*>(wsp->qpc.p), d_Q, d_bad);
+    LF_CUDA(c, cudaGetLastError());
+    c->launches++;
+    return 0;
+  };
+  auto body = [&]() -> int {
+    LF_TRY(a1());
+    auto loop = make_sliced<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks, rg, lo);
+    LF_TRY(loop->advance(ds.n_steps));
+    return loop->finish();
+  };
 
   // CUDA graph of the whole solve (one launch instead of ~p N), replayed while
-  // the problem, the batch and the buffers stay the same.
-  const bool use_graph = c->graphs && !c->profiling && st != nullptr;
-  if (!use_graph) return body();
+  // the problem, the batch and the buffers stay the same.  Very long solves
+  // (more than kGraphMaxKernels kernels) launch directly: their graphs would
+  // take seconds and gigabytes of host memory to build, and their kernels
+  // outlast the launch cost anyway.
+  const int64_t inner_per_step = n_R == 0 ? 0 : (cps >= 2000 ? 1 : (cps >= 1000 ? 8 * (p - 1) : p - 1));
+  const int64_t est_kernels = ds.n_steps * (1 + inner_per_step);
+  const bool use_graph = c->graphs && !c->profiling && st != nullptr && est_kernels <= kGraphMaxKernels;
+  if (!use_graph) {
+    if (!defer) return body();
+    LF_TRY(a1());
+    *defer = make_sliced<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks, rg, lo);
+    return 0;
+  }
   GraphKey key;
   std::memset(&key, 0, sizeof(key));  // padding too: keys compare bytewise
   key.mesh = ds.mesh_id;
@@ -742,6 +1038,9 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   key.f0 = ds.src_f0;
   key.t0 = ds.src_t0;
   key.famp = ds.src_amp;
+  key.ragged = rg ? rg->hash : 0;
+  key.dts = rg ? rg->d_dts : nullptr;
+  key.sig = rg ? rg->d_sig : nullptr;
   for (auto& ge : ws.graphs)
     if (ge.key == key) {
       LF_CUDA(c, cudaGraphLaunch(ge.exec, st));
@@ -774,15 +1073,16 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
 
 template <typename Real>
 int run_solve(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64_t S, double* d_Q,
-              double* d_uN, Workspace& ws, cudaStream_t st) {
+              double* d_uN, Workspace& ws, cudaStream_t st, std::unique_ptr<SliceTask>* defer,
+              const RaggedSpec* rg) {
   MeshGPU& mg = *c->meshes[ds.mesh_id];
   const Qoi& q = c->qois[ds.qoi_id];
   const Field& u0 = c->fields[ds.u0_field];
   const Field* v0 = ds.v0_field >= 0 ? &c->fields[ds.v0_field] : nullptr;
   switch (mg.h.KP) {
-    case 4: return run_solve_kp<Real, 4>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st);
-    case 8: return run_solve_kp<Real, 8>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st);
-    default: return run_solve_kp<Real, 16>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st);
+    case 4: return run_solve_kp<Real, 4>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st, defer, rg);
+    case 8: return run_solve_kp<Real, 8>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st, defer, rg);
+    default: return run_solve_kp<Real, 16>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st, defer, rg);
   }
 }
 
@@ -807,10 +1107,13 @@ int check_desc(lflts_ctx* c, const lflts_solve_desc* ds) {
   return 0;
 }
 
+// defer non-null: a solve that is not captured into a graph only queues its
+// start here and returns its time loop as a SliceTask in *defer.
 int solve_device(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64_t S, double* d_Q,
-                 double* d_uN, Workspace& ws, cudaStream_t st) {
-  if (ds.precision == 32) return run_solve<float>(c, ds, d_xi, S, d_Q, d_uN, ws, st);
-  return run_solve<double>(c, ds, d_xi, S, d_Q, d_uN, ws, st);
+                 double* d_uN, Workspace& ws, cudaStream_t st, std::unique_ptr<SliceTask>* defer = nullptr,
+                 const RaggedSpec* rg = nullptr) {
+  if (ds.precision == 32) return run_solve<float>(c, ds, d_xi, S, d_Q, d_uN, ws, st, defer, rg);
+  return run_solve<double>(c, ds, d_xi, S, d_Q, d_uN, ws, st, defer, rg);
 }
 
 Workspace& workspace(lflts_ctx* c, size_t slot) {
@@ -872,6 +1175,8 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
   LF_TRY(ensure(c, gb.rho, size_t(std::max(p - 1, 1)) * rsz));
   LF_TRY(ensure(c, gb.gs, rsz));
   LF_TRY(ensure(c, gb.A, size_t(std::max<int64_t>(h.n_edges, 1)) * S * sizeof(double)));
+  constexpr bool kF32 = std::is_same<Real, float>::value;  // FP32 edge terms, per-segment FP32 sums
+  if (kF32) LF_TRY(ensure(c, gb.Aseg, size_t(std::max<int64_t>(h.n_edges, 1)) * S * sizeof(float)));
   LF_TRY(ensure(c, gb.nua, state));
   LF_TRY(ensure(c, gb.nub, state));
   LF_TRY(ensure(c, gb.dnu, state));
@@ -925,7 +1230,8 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
     const int tb = static_cast<int>(std::min<int64_t>(S, 128));
     Prof pr(c, st);
     k_qoi_partial<Real><<<dim3(n_chunks, static_cast<unsigned>((S + tb - 1) / tb)), tb, 0, st>>>(
-        uc, (int)S, q.idx, q.g, q.nnz, chunk, static_cast<double*>(ws.qps.p), static_cast<double*>(ws.qpc.p));
+        uc, (int)S, q.idx, q.g, q.nnz, chunk, static_cast<double*>(ws.qps.p), static_cast<double*>(ws.qpc.p), 0,
+        (int)S);
     LF_CUDA(c, cudaGetLastError());
     k_qoi_final<<<blocks_for(S, 128, 1 << 20), 128, 0, st>>>(n_chunks, (int)S, static_cast<double*>(ws.qps.p),
                                                             static_cast<double*>(ws.qpc.p), d_Q, c->d_bad);
@@ -942,13 +1248,18 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
   LF_CUDA(c, cudaMemsetAsync(vn, 0, state, st));
   LF_CUDA(c, cudaMemsetAsync(dv, 0, state, st));
   LF_CUDA(c, cudaMemsetAsync(A, 0, size_t(std::max<int64_t>(h.n_edges, 1)) * S * sizeof(double), st));
+  float* Aseg = static_cast<float*>(gb.Aseg.p);
+  if (kF32) LF_CUDA(c, cudaMemsetAsync(Aseg, 0, size_t(std::max<int64_t>(h.n_edges, 1)) * S * sizeof(float), st));
   // the step kernels write free nodes only: Dirichlet rows of the recomputed
   // states must hold 0 (the edge accumulation reads them)
   LF_CUDA(c, cudaMemsetAsync(segU, 0, size_t(k) * state, st));
-  k_adj_seed<Real><<<blocks_for(int64_t(q.nnz) * S, 256, c->sms * 16), 256, 0, st>>>(
-      q.nnz, (int)S, q.idx, q.g, mg.minv64, (int)h.n_free, vc, dv);
-  LF_CUDA(c, cudaGetLastError());
-  c->launches++;
+  {
+    Prof pr(c, st);
+    k_adj_seed<Real><<<blocks_for(int64_t(q.nnz) * S, 256, c->sms * 16), 256, 0, st>>>(
+        q.nnz, (int)S, q.idx, q.g, mg.minv64, (int)h.n_free, vc, dv);
+    LF_CUDA(c, cudaGetLastError());
+    pr.end(LFLTS_KERNEL_GRAD, double(q.nnz) * S * 2.0 * rb);
+  }
 
   MeshDev<Real> mdR = Sel<Real>::mesh(mg, n_R);
   mdR.n_free = n_R;  // g = a(u) on R only
@@ -959,6 +1270,18 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
   kc.gamma = stp.gamma;
   kc.c[0] = stp.c0;
   for (int m = 1; m < p; ++m) kc.c[m] = stp.cm[m];
+  // algorithmic bytes per launch (profiling): R rows and edges with an R endpoint
+  // (R is the index prefix [0, n_R) and edge_i < edge_j)
+  int64_t n_edges_R = 0;
+  for (int64_t e = 0; e < h.n_edges; ++e) n_edges_R += h.edge_i[e] < n_R;
+  const double Srb = double(S) * rb;
+  const double edgeP_bytes = double(h.n_edges_P) * Srb;
+  const double edges_bytes = (kF32 ? 8.0 : 16.0) * double(h.n_edges) * S + 2.0 * double(h.n_free) * Srb +
+                             double(2 * p - 2) * double(n_R) * Srb;
+  const Geo gE32 = geometry(c, std::max<int64_t>(h.n_edges, 1), S / VEC);
+  AdjConsts32 kc32{};
+  kc32.p = p;
+  for (int m = 0; m < p; ++m) kc32.c[m] = float(kc.c[m]);
 
   // ---- segments, last to first ------------------------------------------------
   for (int64_t seg = n_ck - 1; seg >= 0; --seg) {
@@ -972,20 +1295,25 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
       const Real* u_n = segU + (n - n0) * sn;
       if (n_R > 0) {
         // (i) g = a(u_n) on R; (ii) r_2 .. r_{p-1} of the inner recursion
-        k_coarse<Real, VEC><<<gR.grid, 256, 0, st>>>(mdR, (int)S, gR.SB, W, u_n, nullptr, nullptr, gs, Real(0),
-                                                      stp.fw, stp.source_amp(double(n) * ds.dt));
-        LF_CUDA(c, cudaGetLastError());
-        c->launches++;
+        {
+          Prof pr(c, st);
+          k_coarse<Real, VEC><<<gR.grid, 256, 0, st>>>(mdR, (int)S, gR.SB, W, u_n, nullptr, nullptr, gs, Real(0),
+                                                        stp.fw, stp.source_amp(double(n) * ds.dt), (int)S,
+                                                        RaggedF{});
+          LF_CUDA(c, cudaGetLastError());
+          pr.end(LFLTS_KERNEL_ADJ_INNER, 2.0 * double(n_R) * Srb + double(n_edges_R) * Srb);
+        }
         for (int m = 1; m <= p - 2; ++m) {
+          Prof pr(c, st);
           const Real* cur = (m == 1) ? gs : rs + (m - 2) * rn;
           const Real s_cur = (m == 1) ? (Real)(-stp.c0) : Real(1);
           const Real* prv = (m == 1) ? nullptr : ((m == 2) ? gs : rs + (m - 3) * rn);
           const Real s_prv = (m == 2) ? (Real)(-stp.c0) : Real(1);
           k_inner<Real, VEC, false><<<gR.grid, 256, 0, st>>>(
               stp.md, (int)S, gR.SB, W, cur, s_cur, prv, s_prv, rs + (m - 1) * rn, gs, nullptr, nullptr, nullptr,
-              (Real)(1.0 + stp.beta[m]), (Real)stp.beta[m], (Real)stp.cm[m], Real(0));
+              (Real)(1.0 + stp.beta[m]), (Real)stp.beta[m], (Real)stp.cm[m], Real(0), (int)S);
           LF_CUDA(c, cudaGetLastError());
-          c->launches++;
+          pr.end(LFLTS_KERNEL_ADJ_INNER, double(m == 1 ? 2 : (m == 2 ? 3 : 4)) * double(n_R) * Srb + edgeP_bytes);
         }
         // (iii) inner adjoint rho_{p-1} .. rho_1 (rho_p = kappa nu_{n+1})
         for (int m = p - 1; m >= 1; --m) {
@@ -994,19 +1322,30 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
           const Real* s2p = (m + 2 == p) ? vc : ((m + 2 < p) ? rho + (m + 1) * rn : nullptr);
           const Real s2 = (m + 2 == p) ? kappa : Real(1);
           const Real b1 = (m + 1 <= p - 1) ? (Real)stp.beta[m + 1] : Real(0);
+          Prof pr(c, st);
           k_adj_inner<Real, VEC><<<gR.grid, 256, 0, st>>>(stp.md, (int)S, gR.SB, W, s1p, s1, s2p, s2,
                                                            rho + (m - 1) * rn, (Real)(1.0 + stp.beta[m]), b1,
                                                            (Real)stp.cm[m]);
           LF_CUDA(c, cudaGetLastError());
-          c->launches++;
+          pr.end(LFLTS_KERNEL_ADJ_INNER, double(s2p ? 3 : 2) * double(n_R) * Srb + edgeP_bytes);
         }
       }
       // (iv) edge accumulators
       kc.kappa = double(kappa);
-      k_adj_edges<Real><<<gE.grid, 256, 0, st>>>(h.n_edges, nP_eff, n_R, (int)S, gE.SB, mg.ends, u_n, vc, gs, rs,
-                                                 rho, A, kc);
-      LF_CUDA(c, cudaGetLastError());
-      c->launches++;
+      {
+        Prof pr(c, st);
+        if constexpr (kF32) {
+          kc32.kappa = float(kappa);
+          kc32.gk = float(kc.gamma * double(kappa));
+          k_adj_edges32<VEC><<<gE32.grid, 256, 0, st>>>(h.n_edges, nP_eff, n_R, (int)S, gE32.SB, mg.ends, u_n, vc,
+                                                        gs, rs, rho, Aseg, kc32);
+        } else {
+          k_adj_edges<Real><<<gE.grid, 256, 0, st>>>(h.n_edges, nP_eff, n_R, (int)S, gE.SB, mg.ends, u_n, vc, gs,
+                                                     rs, rho, A, kc);
+        }
+        LF_CUDA(c, cudaGetLastError());
+        pr.end(LFLTS_KERNEL_ADJ_EDGES, edges_bytes);
+      }
       // (v) nu_n = 2 T nu_{n+1} - nu_{n+2}
       if (n > 0) {
         const Real* fw_saved = stp.fw;
@@ -1017,6 +1356,13 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
         std::swap(vc, vn);
       }
     }
+    if constexpr (kF32) {  // end of the segment: A += Aseg, Aseg = 0
+      const int64_t ne = std::max<int64_t>(h.n_edges, 1) * S;
+      Prof pr(c, st);
+      k_adj_fold<<<blocks_for(ne, 256, c->sms * 16), 256, 0, st>>>(ne, Aseg, A);
+      LF_CUDA(c, cudaGetLastError());
+      pr.end(LFLTS_KERNEL_ADJ_EDGES, 24.0 * double(ne));
+    }
   }
 
   // ---- dQ/dxi_k = sum_edges A_e dK_e/dxi_k ------------------------------------
@@ -1024,13 +1370,15 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
   const int64_t n_chunks = std::max<int64_t>(1, (h.n_edges + chunk - 1) / chunk);
   LF_TRY(ensure(c, gb.part, size_t(n_chunks) * S * h.K * sizeof(double)));
   const int tb = static_cast<int>(std::min<int64_t>(S, 128));
+  Prof pr(c, st);
   k_grad_contract<KP><<<dim3(static_cast<unsigned>(n_chunks), static_cast<unsigned>((S + tb - 1) / tb)), tb, 0, st>>>(
       h.n_edges, (int)S, chunk, mg.ee, mg.eg64, mg.psi64, d_xi, h.K, A, static_cast<double*>(gb.part.p));
   LF_CUDA(c, cudaGetLastError());
   k_grad_finish<<<blocks_for(S * h.K, 128, 1 << 20), 128, 0, st>>>((int)n_chunks, (int)S, h.K,
                                                                    static_cast<double*>(gb.part.p), d_G);
   LF_CUDA(c, cudaGetLastError());
-  c->launches += 2;
+  c->launches++;
+  pr.end(LFLTS_KERNEL_GRAD, 8.0 * double(h.n_edges) * S + 8.0 * double(S) * h.K * (1.0 + n_chunks));
   return 0;
 }
 
@@ -1068,7 +1416,7 @@ int lflts_internal_set_error(lflts_ctx* ctx, int code, const char* msg) {
 // ============================================================================
 extern "C" {
 
-int lflts_version(void) { return 100; }
+int lflts_version(void) { return 200; }
 
 int lflts_create(lflts_ctx** out, int device) {
   if (!out) return LFLTS_ERR_ARG;
@@ -1343,28 +1691,38 @@ int lflts_run_pairs(lflts_ctx* c, const lflts_pair_job* jobs, int n_jobs, int me
   if (mem != LFLTS_MEM_HOST && mem != LFLTS_MEM_DEVICE) return fail(c, LFLTS_ERR_ARG, "run_pairs: bad mem kind");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-  // ---- group identical solves ----------------------------------------------
+  // ---- group the solves ------------------------------------------------------
+  // Solves that differ at most in (dt, n_steps) share a batch: identical ones
+  // form a segment, and a batch with several segments is ragged (each draw
+  // steps with its own dt for its own count; segments sorted by step count).
   struct Member { int job; bool fine; int64_t off; };
-  struct Group { lflts_solve_desc desc; int64_t S = 0; std::vector<Member> members; };
+  struct Seg { lflts_solve_desc desc; int64_t S = 0; std::vector<Member> members; };
+  struct Group { std::vector<Seg> segs; int64_t S = 0; };
   std::vector<Group> groups;
-  auto key_eq = [](const lflts_solve_desc& a, const lflts_solve_desc& b) {
+  auto same_batch = [](const lflts_solve_desc& a, const lflts_solve_desc& b) {
     return a.mesh_id == b.mesh_id && a.qoi_id == b.qoi_id && a.u0_field == b.u0_field &&
            a.v0_field == b.v0_field && a.precision == b.precision && a.p == b.p && a.nu == b.nu &&
-           a.dt == b.dt && a.n_steps == b.n_steps && a.source_id == b.source_id && a.src_f0 == b.src_f0 &&
-           a.src_t0 == b.src_t0 && a.src_amp == b.src_amp;
+           a.source_id == b.source_id && a.src_f0 == b.src_f0 && a.src_t0 == b.src_t0 && a.src_amp == b.src_amp;
   };
   auto add_member = [&](const lflts_solve_desc& ds, int j, bool fine, int64_t S) {
+    Group* gp = nullptr;
     for (auto& gr : groups)
-      if (key_eq(gr.desc, ds)) {
-        gr.members.push_back({j, fine, gr.S});
-        gr.S += S;
-        return;
-      }
-    Group gr;
-    gr.desc = ds;
-    gr.members.push_back({j, fine, 0});
-    gr.S = S;
-    groups.push_back(gr);
+      if (same_batch(gr.segs[0].desc, ds)) gp = &gr;
+    if (!gp) {
+      groups.emplace_back();
+      gp = &groups.back();
+    }
+    Seg* sp = nullptr;
+    for (auto& sg : gp->segs)
+      if (sg.desc.dt == ds.dt && sg.desc.n_steps == ds.n_steps) sp = &sg;
+    if (!sp) {
+      gp->segs.emplace_back();
+      sp = &gp->segs.back();
+      sp->desc = ds;
+    }
+    sp->members.push_back({j, fine, sp->S});
+    sp->S += S;
+    gp->S += S;
   };
   for (int j = 0; j < n_jobs; ++j) {
     const lflts_pair_job& jb = jobs[j];
@@ -1380,6 +1738,29 @@ int lflts_run_pairs(lflts_ctx* c, const lflts_pair_job* jobs, int n_jobs, int me
   }
   for (auto& gr : groups)
     if (gr.S > kMaxS) return fail(c, LFLTS_ERR_ARG, "run_pairs: merged batch larger than 2097120 samples");
+  // segments by step count (descending), members' offsets within the batch
+  std::vector<RaggedSpec> specs(groups.size());
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    Group& gr = groups[gi];
+    std::stable_sort(gr.segs.begin(), gr.segs.end(),
+                     [](const Seg& a, const Seg& b) { return a.desc.n_steps > b.desc.n_steps; });
+    int64_t off = 0;
+    uint64_t hsh = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+      for (int b = 0; b < 8; ++b) hsh = (hsh ^ ((v >> (8 * b)) & 0xff)) * 1099511628211ull;
+    };
+    for (Seg& sg : gr.segs) {
+      for (Member& mb : sg.members) mb.off += off;
+      specs[gi].segs.push_back({off, sg.S, sg.desc.n_steps, sg.desc.dt});
+      uint64_t dbits = 0;
+      std::memcpy(&dbits, &sg.desc.dt, sizeof(dbits));
+      mix(uint64_t(sg.desc.n_steps));
+      mix(uint64_t(sg.S));
+      mix(dbits);
+      off += sg.S;
+    }
+    specs[gi].hash = hsh;
+  }
 
   // ---- streams and events ----------------------------------------------------
   const size_t ng = groups.size();
@@ -1397,22 +1778,70 @@ int lflts_run_pairs(lflts_ctx* c, const lflts_pair_job* jobs, int n_jobs, int me
   LF_CUDA(c, cudaEventRecord(c->sync_events[ng], st));
 
   // ---- per group: gather xi, solve ------------------------------------------
+  // Groups captured into graphs are queued whole; the time loops of the
+  // others are queued in slices of kSliceSteps outer steps, group after
+  // group, so that every stream keeps work queued.  With per-launch
+  // profiling on, every group is queued whole (its kernels then rarely share
+  // the GPU with another group's, so their event times stay their own).
+  std::vector<std::unique_ptr<SliceTask>> tasks(ng);
+  const bool slice = !c->profiling;
   for (size_t gi = 0; gi < ng; ++gi) {
     Group& gr = groups[gi];
     Workspace& ws = workspace(c, 1 + gi);
-    const int K = c->meshes[gr.desc.mesh_id]->h.K;
+    const lflts_solve_desc& gd = gr.segs[0].desc;  // the longest segment: dt_ref and the step count
+    const int K = c->meshes[gd.mesh_id]->h.K;
     cudaStream_t gs = c->streams[gi];
     LF_CUDA(c, cudaStreamWaitEvent(gs, c->sync_events[ng], 0));
     LF_TRY(ensure(c, ws.xraw, size_t(gr.S) * K * sizeof(double)));
     LF_TRY(ensure(c, ws.Q, size_t(gr.S) * sizeof(double)));
-    for (const Member& mb : gr.members) {
-      const lflts_pair_job& jb = jobs[mb.job];
-      LF_CUDA(c, cudaMemcpyAsync(static_cast<double*>(ws.xraw.p) + mb.off * K, jb.xi, size_t(jb.S) * K * sizeof(double),
-                                 mem == LFLTS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, gs));
+    for (const Seg& sg : gr.segs)
+      for (const Member& mb : sg.members) {
+        const lflts_pair_job& jb = jobs[mb.job];
+        LF_CUDA(c, cudaMemcpyAsync(static_cast<double*>(ws.xraw.p) + mb.off * K, jb.xi,
+                                   size_t(jb.S) * K * sizeof(double),
+                                   mem == LFLTS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, gs));
+      }
+    const RaggedSpec* rg = nullptr;
+    if (gr.segs.size() > 1) {  // per-draw dt and weight scale of the ragged batch
+      const size_t rb = gd.precision == 32 ? sizeof(float) : sizeof(double);
+      ws.h_dts.assign(size_t(gr.S), 0.0);
+      ws.h_sig.assign(size_t(gr.S) * rb, 0);
+      for (const RaggedSeg& sg : specs[gi].segs)
+        for (int64_t k = 0; k < sg.cnt; ++k) {
+          const double sc = (sg.dt / gd.dt) * (sg.dt / gd.dt);
+          ws.h_dts[size_t(sg.off + k)] = sg.dt;
+          if (rb == sizeof(float)) {
+            const float f = float(sc);
+            std::memcpy(ws.h_sig.data() + size_t(sg.off + k) * rb, &f, rb);
+          } else {
+            std::memcpy(ws.h_sig.data() + size_t(sg.off + k) * rb, &sc, rb);
+          }
+        }
+      LF_TRY(ensure(c, ws.dts, size_t(gr.S) * sizeof(double)));
+      LF_TRY(ensure(c, ws.sig, size_t(gr.S) * rb));
+      LF_CUDA(c, cudaMemcpyAsync(ws.dts.p, ws.h_dts.data(), size_t(gr.S) * sizeof(double), cudaMemcpyHostToDevice, gs));
+      LF_CUDA(c, cudaMemcpyAsync(ws.sig.p, ws.h_sig.data(), size_t(gr.S) * rb, cudaMemcpyHostToDevice, gs));
+      specs[gi].d_dts = static_cast<const double*>(ws.dts.p);
+      specs[gi].d_sig = ws.sig.p;
+      rg = &specs[gi];
     }
-    LF_TRY(solve_device(c, gr.desc, static_cast<double*>(ws.xraw.p), gr.S, static_cast<double*>(ws.Q.p), nullptr, ws, gs));
-    LF_CUDA(c, cudaEventRecord(c->sync_events[gi], gs));
+    LF_TRY(solve_device(c, gd, static_cast<double*>(ws.xraw.p), gr.S, static_cast<double*>(ws.Q.p), nullptr, ws,
+                        gs, slice ? &tasks[gi] : nullptr, rg));
+    if (!tasks[gi]) LF_CUDA(c, cudaEventRecord(c->sync_events[gi], gs));
   }
+  for (bool more = true; more;) {
+    more = false;
+    for (size_t gi = 0; gi < ng; ++gi)
+      if (tasks[gi] && !tasks[gi]->done()) {
+        LF_TRY(tasks[gi]->advance(kSliceSteps));
+        more = more || !tasks[gi]->done();
+      }
+  }
+  for (size_t gi = 0; gi < ng; ++gi)
+    if (tasks[gi]) {
+      LF_TRY(tasks[gi]->finish());
+      LF_CUDA(c, cudaEventRecord(c->sync_events[gi], c->streams[gi]));
+    }
   for (size_t gi = 0; gi < ng; ++gi) LF_CUDA(c, cudaStreamWaitEvent(st, c->sync_events[gi], 0));
 
   // ---- per job: dQ, Qf and level sums on the caller's stream ----------------
@@ -1426,12 +1855,13 @@ int lflts_run_pairs(lflts_ctx* c, const lflts_pair_job* jobs, int n_jobs, int me
     const double* qf = nullptr;
     const double* qc = nullptr;
     for (size_t gi = 0; gi < ng; ++gi)
-      for (const Member& mb : groups[gi].members)
-        if (mb.job == j) {
-          const double* base = static_cast<double*>(workspace(c, 1 + gi).Q.p) + mb.off;
-          if (mb.fine) qf = base;
-          else qc = base;
-        }
+      for (const Seg& sg : groups[gi].segs)
+        for (const Member& mb : sg.members)
+          if (mb.job == j) {
+            const double* base = static_cast<double*>(workspace(c, 1 + gi).Q.p) + mb.off;
+            if (mb.fine) qf = base;
+            else qc = base;
+          }
     double* dq_dst = jb.dQ;
     double* qf_dst = jb.Qf;
     double* sums_dst = jb.sums;
@@ -1542,6 +1972,11 @@ int lflts_set_option(lflts_ctx* c, int option, int64_t value) {
       if (value < 1024) return fail(c, LFLTS_ERR_ARG, "set_option: block budget below 1024 bytes");
       c->block_budget = double(value);
       for (auto& m : c->meshes) m->blocks.clear();  // device lists stay owned by the context
+      return LFLTS_OK;
+    case LFLTS_OPT_FUSED_INNER:
+      if (value < 0 || value > 2) return fail(c, LFLTS_ERR_ARG, "set_option: fused inner mode must be 0, 1 or 2");
+      c->fused_mode = static_cast<int>(value);
+      for (auto& m : c->meshes) m->tuned.clear();  // re-tune with the new candidate set
       return LFLTS_OK;
     default: return fail(c, LFLTS_ERR_ARG, "set_option: unknown option");
   }

@@ -29,7 +29,8 @@ LFLTS_ERR_TIMEOUT = -5
 LFLTS_ERR_MESH = -6
 LFLTS_MEM_HOST = 0
 LFLTS_MEM_DEVICE = 1
-KERNEL_CLASSES = {"init": 0, "coarse": 1, "inner": 2, "qoi": 3, "sums": 4}
+KERNEL_CLASSES = {"init": 0, "coarse": 1, "inner": 2, "qoi": 3, "sums": 4,
+                  "adj_inner": 5, "adj_edges": 6, "grad": 7}
 
 EXPORTED = [
     "lflts_version", "lflts_create", "lflts_destroy", "lflts_last_error", "lflts_mesh_add",
@@ -43,6 +44,7 @@ LFLTS_OPT_GRAPHS = 1
 LFLTS_OPT_AUTOTUNE = 2
 LFLTS_OPT_BLOCKED = 3
 LFLTS_OPT_BLOCK_BUDGET = 4
+LFLTS_OPT_FUSED_INNER = 5
 
 
 class LibraryNotBuilt(RuntimeError):

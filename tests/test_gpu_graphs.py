@@ -105,3 +105,89 @@ def test_l2_blocked_inner_loop_bit_identical(lf, prec, p):
     for k, (Q, U) in out.items():
         np.testing.assert_array_equal(U, ref[1])
         np.testing.assert_array_equal(Q, ref[0])
+
+
+def _launches(lf, ctx):
+    return lf.lflts_launch_count(ctx.h)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("p", [2, 3, 5, 9])
+@pytest.mark.parametrize("S", [40, 33, 130])
+def test_fused_inner_kernel_bit_identical(lf, prec, p, S):
+    """All p-1 inner substeps in one launch (R and the CTA's draws in shared
+    memory) give the same values, bit for bit, as one launch per substep;
+    ragged batches (S odd: one draw per thread) included, with a source."""
+    from workload import point_source
+    lev = small_level(n=16, p=p, K=4, box=(0.375, 0.625, 0.375, 0.625))
+    nodes, w = point_source(lev["mesh"], (0.5, 0.52))
+    lev = dict(lev, source={"nodes": nodes, "weights": w, "f0": 5.0, "t0": 0.2, "amp": 1.0})
+    xi = draws(S, 4, seed=100 + p + S)
+    out, launches = {}, {}
+    for mode in (0, 2):
+        ctx = lf.Context(0)
+        try:
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_AUTOTUNE, 0)
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_FUSED_INNER, mode)
+            h = ctx.add_level(lev)
+            n0 = _launches(lf, ctx)
+            out[mode] = ctx.solve(h, xi, precision=prec, state=True)
+            launches[mode] = _launches(lf, ctx) - n0
+            n_steps = h.n_steps
+        finally:
+            ctx.close()
+    np.testing.assert_array_equal(out[2][1], out[0][1])
+    np.testing.assert_array_equal(out[2][0], out[0][0])
+    # one coarse and one fused launch per step instead of 1 + (p - 1)
+    assert launches[0] - launches[2] == n_steps * (p - 2)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_fused_inner_kernel_graded_lshape(lf, prec):
+    """The graded L-shape (tiny R at the reentrant corner, p = 3 and 5, Ricker
+    source): the fused path equals the per-substep path bit for bit, and the
+    autotuner's choice (fused or not) changes nothing."""
+    from workload import CONFIG_LSHAPE, lshape_level, xi_gaussian
+    cfg = CONFIG_LSHAPE
+    for l in (0, 1):
+        lev = lshape_level(cfg, l, m0=6)
+        lev = dict(lev, T=0.3, dt=0.3 / 400, n_steps=400)
+        xi = xi_gaussian(cfg.seed, l, 24, cfg.K, cfg.sigma)
+        out = {}
+        for mode, tune in ((0, 0), (2, 0), (1, 1)):
+            ctx = lf.Context(0)
+            try:
+                lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_AUTOTUNE, tune)
+                lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_FUSED_INNER, mode)
+                h = ctx.add_level(lev)
+                out[(mode, tune)] = ctx.solve(h, xi, precision=prec, state=True)
+            finally:
+                ctx.close()
+        for k, (Q, U) in out.items():
+            np.testing.assert_array_equal(U, out[(0, 0)][1])
+            np.testing.assert_array_equal(Q, out[(0, 0)][0])
+
+
+def test_long_solves_launch_without_graph(lf):
+    """Solves of more than 120,000 kernels launch directly instead of being
+    captured into a graph; shorter solves on a stream are captured."""
+    import torch
+    lev = small_level(n=8, p=2, K=4, box=(0.375, 0.625, 0.375, 0.625))
+    xi = torch.from_numpy(draws(8, 4, seed=5)).cuda()
+    ctx = lf.Context(0)
+    st = torch.cuda.Stream()
+    try:
+        lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_AUTOTUNE, 0)
+        lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_FUSED_INNER, 0)
+        h = ctx.add_level(lev)
+        q = torch.zeros(8, dtype=torch.float64, device="cuda")
+        for n_steps, graphed in ((1000, True), (61000, False)):
+            d = h.desc(32)
+            d.n_steps = n_steps
+            g0 = lf.lflts_get_stats(ctx.h)["graph_launches"]
+            lf.lflts_solve(ctx.h, d, xi, 8, q, None, lf.LFLTS_MEM_DEVICE, st.cuda_stream)
+            st.synchronize()
+            assert (lf.lflts_get_stats(ctx.h)["graph_launches"] - g0 == 1) == graphed
+            assert torch.isfinite(q).all()
+    finally:
+        ctx.close()

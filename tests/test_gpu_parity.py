@@ -204,20 +204,28 @@ def test_bad_arguments_rejected(lf, ctx):
         lf.lflts_solve(ctx.h, bad, draws(2, 4), 2, np.zeros(2))
 
 
-def test_profiling_counters(lf, ctx):
+@pytest.mark.parametrize("fused", [0, 2])
+def test_profiling_counters(lf, ctx, fused):
+    """Per-class launch counts: p - 1 inner launches per step, or one with the
+    fused inner kernel; init 3 kernels, QoI 2."""
     lev = small_level(n=12, p=4, K=4)
     h = ctx.add_level(lev)
-    lf.lflts_profile_reset(ctx.h)
-    lf.lflts_profile_enable(ctx.h, True)
-    n0 = lf.lflts_launch_count(ctx.h)
-    ctx.solve(h, draws(8, 4), precision=32)
-    lf.lflts_profile_enable(ctx.h, False)
-    co = lf.lflts_profile_read(ctx.h, "coarse")
-    inn = lf.lflts_profile_read(ctx.h, "inner")
-    assert co["launches"] == h.n_steps
-    assert inn["launches"] == h.n_steps * 3
-    assert co["ms"] > 0 and inn["alg_bytes"] > 0
-    assert lf.lflts_launch_count(ctx.h) - n0 == 3 + h.n_steps * 4 + 2
+    lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_FUSED_INNER, fused)
+    try:
+        lf.lflts_profile_reset(ctx.h)
+        lf.lflts_profile_enable(ctx.h, True)
+        n0 = lf.lflts_launch_count(ctx.h)
+        ctx.solve(h, draws(8, 4), precision=32)
+        lf.lflts_profile_enable(ctx.h, False)
+        co = lf.lflts_profile_read(ctx.h, "coarse")
+        inn = lf.lflts_profile_read(ctx.h, "inner")
+        per_step = 3 if fused == 0 else 1
+        assert co["launches"] == h.n_steps
+        assert inn["launches"] == h.n_steps * per_step
+        assert co["ms"] > 0 and inn["alg_bytes"] > 0
+        assert lf.lflts_launch_count(ctx.h) - n0 == 3 + h.n_steps * (1 + per_step) + 2
+    finally:
+        lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_FUSED_INNER, 1)
 
 
 @pytest.mark.parametrize("precision", [64, 32])
