@@ -359,14 +359,16 @@ Geo geometry_vec(const lflts_ctx* c, int64_t n, int64_t S, int vec, int cta_per_
 
 // Plan of the fused inner kernel (all substeps of a step in one launch, R in
 // shared memory): lanes per node SBf (draw slab SL = SBf vec) and dynamic
-// shared memory; smem = 0 when R does not fit.  The slab widens while R is
-// small against the CTA and the batch still gives two CTAs per SM.
+// shared memory; smem = 0 when R does not fit.
 constexpr size_t kFusedSmemMax = 200 * 1024;
 inline void fused_plan(const lflts_ctx* c, int n_R, int64_t S, int vec, size_t rb, int& SBf, size_t& smem) {
+  (void)c;
   SBf = 1;
   smem = 0;
   if (n_R < 1) return;
-  while (SBf < 8 && int64_t(n_R) * SBf * 2 <= 256 && (S / (int64_t(SBf) * 2 * vec)) >= 2 * c->sms) SBf *= 2;
+  // lanes per node: fill the 256 threads of a CTA when R is small (the
+  // kernels of a step are short; fewer, fuller CTAs load less index data)
+  while (SBf < 8 && int64_t(n_R) * SBf * 2 <= 256 && int64_t(SBf) * 2 * vec <= S) SBf *= 2;
   const size_t need = 4 * size_t(n_R) * size_t(SBf) * size_t(vec) * rb;
   if (need <= kFusedSmemMax) smem = need;
 }
@@ -542,9 +544,9 @@ struct Stepper {
       const RaggedF rf = ragged(n);
 #define LF_COARSE(B, RG) \
   k_coarse<Real, VEC, B, RG><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg, fw, fa, (int)S_act, rf)
-      if (dts) {  // ragged batch
+      if (dts) {  // ragged batch (bounded to 64 registers: four CTAs of 256 per SM)
         if (minb6) LF_COARSE(6, true);
-        else LF_COARSE(1, true);
+        else LF_COARSE(4, true);
       } else {
         if (minb6) LF_COARSE(6, false);
         else LF_COARSE(1, false);
@@ -613,10 +615,11 @@ struct Stepper {
 template <typename Real, int VEC>
 int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S,
               Workspace& ws, Real*& uc_out, cudaStream_t st, int cta_per_sm = 16, int64_t n_steps = -1,
-              const MeshGPU::DevBlocks* blocks = nullptr) {
+              const MeshGPU::DevBlocks* blocks = nullptr, const double* dts = nullptr) {
   Stepper<Real, VEC> stp(c, ds, mg, n_R, S, static_cast<const Real*>(ws.W.p), static_cast<Real*>(ws.g.p),
                          static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p),
                          cta_per_sm);
+  stp.dts = dts;  // a ragged batch: its kernels (all draws active)
   if (blocks && cta_per_sm >= 1000 && cta_per_sm < 2000) {
     stp.blk = &blocks->h;
     stp.blk_nodes = blocks->d_nodes;
@@ -673,10 +676,10 @@ int get_blocks(lflts_ctx* c, MeshGPU& mg, int64_t S, int p, const MeshGPU::DevBl
 template <typename Real>
 int time_loop_vec(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
                   Real*& uc, cudaStream_t st, int vec, int cps, int64_t n_steps = -1,
-                  const MeshGPU::DevBlocks* blocks = nullptr) {
-  if (vec == 4) return time_loop<Real, 4>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks);
-  if (vec == 2) return time_loop<Real, 2>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks);
-  return time_loop<Real, 1>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks);
+                  const MeshGPU::DevBlocks* blocks = nullptr, const double* dts = nullptr) {
+  if (vec == 4) return time_loop<Real, 4>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks, dts);
+  if (vec == 2) return time_loop<Real, 2>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks, dts);
+  return time_loop<Real, 1>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks, dts);
 }
 
 // Whether the fused inner kernel can run this batch; raises its dynamic
@@ -817,7 +820,7 @@ std::unique_ptr<SliceTask> make_sliced(lflts_ctx* c, const lflts_solve_desc& ds,
 // (the state is re-initialised afterwards) and keeps the fastest.
 template <typename Real>
 int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
-                 cudaStream_t st, int& vec, int& cps, const MeshGPU::DevBlocks* blocks) {
+                 cudaStream_t st, int& vec, int& cps, const MeshGPU::DevBlocks* blocks, const double* dts) {
   const int vmax = (sizeof(Real) == 4) ? 4 : 2;
   std::vector<int> vecs;
   for (int v = vmax; v >= 1; v /= 2)
@@ -855,9 +858,9 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
       for (int k : {8, 16, 32, 108, 116, 132}) shapes.push_back(2000 + k);
     for (int k : shapes) {
       Real* uc = nullptr;
-      int rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, 1, blocks);  // warm
+      int rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, 1, blocks, dts);  // warm
       if (!rc) rc = cudaEventRecord(e0, st) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
-      if (!rc) rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, steps, blocks);
+      if (!rc) rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, steps, blocks, dts);
       if (!rc) rc = cudaEventRecord(e1, st) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
       if (!rc) rc = cudaEventSynchronize(e1) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
       float ms = 0.f;
@@ -944,11 +947,11 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
     const int rc = a1();  // edge weights and a valid state for the timing runs
     c->profiling = prof;
     LF_TRY(rc);
-    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks));
+    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks, rg ? rg->d_dts : nullptr));
     c->tune_launches += c->launches - l0;
     c->launches = l0;
   } else {
-    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks));
+    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks, rg ? rg->d_dts : nullptr));
   }
   if (c->force_blocked && blocks) cps = 1000 + cps % 1000;
 
