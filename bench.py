@@ -685,11 +685,44 @@ def run_lts_vs_lf(args):
 
 def run_profile_case(args):
     """Small case for ncu captures: a few steps of one batched FP32 mesh solve
-    with the benchmark's launch configuration (level args.profile_case)."""
+    with the benchmark's launch configuration (level args.profile_case); with
+    --config lshape a few steps of one graded L-shape level with the fused
+    inner kernel; with --config adjoint one gradient of a few steps."""
     import torch
     from paper_2106_11117_gb300 import build, lflts
     from workload import level_problem, xi_uniform
     build.build()
+    if args.config == "lshape":
+        from workload import CONFIG_LSHAPE as lc, lshape_level, xi_gaussian
+        l = args.profile_case
+        lev = lshape_level(lc, l)
+        S = args.profile_samples or lc.samples[l]
+        ctx = lflts.Context(0)
+        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_AUTOTUNE, 0)
+        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_FUSED_INNER, 2)
+        h = ctx.add_level(dict(lev, dt=lev["T"] / 200000, n_steps=args.profile_steps))
+        xi = torch.from_numpy(xi_gaussian(lc.seed, l, S, lc.K, lc.sigma)).cuda()
+        Q = torch.zeros(S, dtype=torch.float64, device="cuda")
+        lflts.lflts_solve(ctx.h, h.desc(lc.precision), xi, S, Q, None, lflts.LFLTS_MEM_DEVICE,
+                          torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": f"{lc.name} level {l}", "S": S, "n_steps": args.profile_steps, **h.info}))
+        ctx.close()
+        return
+    if args.config == "adjoint":
+        from workload import CONFIG_ADJOINT as ac
+        S = args.profile_samples or ac.samples[0]
+        ctx = lflts.Context(0)
+        h = ctx.add_level(dict(level_problem(ac, 0), n_steps=args.profile_steps))
+        xi = torch.from_numpy(xi_uniform(ac.seed, 0, S, ac.K)).cuda()
+        Q = torch.zeros(S, dtype=torch.float64, device="cuda")
+        G = torch.zeros(S, ac.K, dtype=torch.float64, device="cuda")
+        lflts.lflts_grad_xi(ctx.h, h.desc(32), xi, S, 64, Q, G, lflts.LFLTS_MEM_DEVICE,
+                            torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": f"{ac.name} gradient", "S": S, "n_steps": args.profile_steps, **h.info}))
+        ctx.close()
+        return
     cfg = _cfg(args.config)
     l = args.profile_case
     S = cfg.samples[l] + (cfg.samples[l + 1] if l + 1 < cfg.levels else 0)

@@ -373,14 +373,17 @@ k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
 // All p-1 inner substeps of one outer step in one launch, for a small R.
 //
 // CTA b owns the draws [b SL, b SL + SL) (SL = SBf VEC) of every R node.
-// g and the recursion r_m of those draws live in shared memory, plane 0 = g
-// (r_1 = -c_0 g is never formed), planes 1..3 = r_2, r_3, ... in rotation,
-// and __syncthreads separates the substeps: the draws of different CTAs
-// never interact, so no grid-wide synchronisation is needed.  Per node the
-// arithmetic is that of k_inner, term by term and in the same order, so the
-// result is the same bit for bit; only the global traffic differs (g, u, d on
-// R and the P-edge weights once per step instead of once per substep).
-// Shared memory: 4 n_R SL sizeof(Real) bytes.
+// Everything the substeps touch is staged in shared memory once: g and the
+// recursion r_m of those draws (plane 0 = g, r_1 = -c_0 g is never formed;
+// planes 1..3 = r_2, r_3, ... in rotation), the coupling slots of R (target
+// and edge weight of the slab's draws, in the order k_inner visits them),
+// their offsets and 1/m.  __syncthreads separates the substeps: the draws of
+// different CTAs never interact, so no grid-wide synchronisation is needed.
+// Per node the arithmetic is that of k_inner, term by term and in the same
+// order (the left-out slots add exact zeros), so the result is the same bit
+// for bit; only the global traffic differs (g, u, d on R and the P-edge
+// weights once per step instead of once per substep).
+// Shared memory: (4 n_R SL + n_slots SL + n_R) Real + (n_slots + n_R + 1) int.
 template <typename Real>
 struct InnerCoef {
   Real opb[64], beta[64], cm[64];  // (1 + beta_m), beta_m, c_m for m = 1..p-1
@@ -388,25 +391,42 @@ struct InnerCoef {
   int p;
 };
 
+__host__ __device__ inline size_t fused_real_count(int nR, int n_slots, int SL) {
+  return (size_t)4 * nR * SL + (size_t)n_slots * SL + (size_t)nR;
+}
+
 template <typename Real, int VEC, bool RAG = false>
 __global__ void __launch_bounds__(256)
 k_inner_fused(MeshDev<Real> m, int S, int SBf, const Real* __restrict__ W, const Real* __restrict__ g,
               const Real* __restrict__ u, Real* __restrict__ u_next, Real* __restrict__ d,
-              const InnerCoef<Real> k, Real kappa, int S_lim) {
+              const InnerCoef<Real> k, Real kappa, int S_lim, const int* __restrict__ rptr,
+              const int2* __restrict__ rslot, int n_slots) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const int SL = SBf * VEC;
   const int nR = m.n_R, nP = m.n_P;
   const size_t plane = (size_t)nR * SL;
+  Real* wsm = sm + 4 * plane;                       // [n_slots][SL]
+  Real* sminv = wsm + (size_t)n_slots * SL;         // [nR]
+  const size_t ioff = (fused_real_count(nR, n_slots, SL) * sizeof(Real) + 15) / 16 * 16;
+  int* sj = reinterpret_cast<int*>(smem_raw + ioff);  // [n_slots]
+  int* sptr = sj + n_slots;                            // [nR + 1]
   const int lane = threadIdx.x % SBf, row = threadIdx.x / SBf, NB = blockDim.x / SBf;
   const int s0 = blockIdx.x * SL + lane * VEC;  // first draw of this thread (VEC divides S)
   const int lim = RAG ? S_lim : S;
   const bool active = s0 < lim;
   const int nvalid = lim - s0;
   const int o = lane * VEC;
-  if (active)
+  if (s0 < S)
     for (int i = row; i < nR; i += NB)
       stp<Real, VEC>(sm + (size_t)i * SL + o, ldp<Real, VEC>(g + (size_t)i * S + s0));
+  for (int t = row; t < n_slots; t += NB) {
+    const int2 q = rslot[t];
+    if (lane == 0) sj[t] = q.x;
+    if (s0 < S) stp<Real, VEC>(wsm + (size_t)t * SL + o, ldp<Real, VEC>(W + (size_t)q.y * S + s0));
+  }
+  for (int t = threadIdx.x; t <= nR; t += blockDim.x) sptr[t] = rptr[t];
+  for (int t = threadIdx.x; t < nR; t += blockDim.x) sminv[t] = m.minv[t];
   __syncthreads();
   const Real* cur = sm;
   Real s_cur = k.neg_c0;
@@ -421,59 +441,36 @@ k_inner_fused(MeshDev<Real> m, int S, int SBf, const Real* __restrict__ W, const
       for (int i = row; i < nR; i += NB) {
         const size_t io = (size_t)i * SL + o;
         const bool iP = i < nP;
-        const Nb4 nb = load_nb4(m, i);
-        const int t0 = m.adj_ptr[i] + 4, t1 = m.adj_ptr[i + 1];
         const Pack<Real, VEC> rc = ldp<Real, VEC>(cur + io);
         const Pack<Real, VEC> gi = ldp<Real, VEC>(sm + io);
-        Pack<Real, VEC> rj[4], w[4], rp;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int j = nb.j[q];
-          const bool jP = j >= 0 && j < nP;
-          if (jP || (iP && j >= 0)) {
-            w[q] = ldp<Real, VEC>(W + (size_t)nb.e[q] * S + s0);
-          } else {
-#pragma unroll
-            for (int kk = 0; kk < VEC; ++kk) w[q].v[kk] = Real(0);
-          }
-          if (jP) {
-            rj[q] = ldp<Real, VEC>(cur + (size_t)j * SL + o);
-          } else {
-#pragma unroll
-            for (int kk = 0; kk < VEC; ++kk) rj[q].v[kk] = Real(0);
-          }
-        }
+        Pack<Real, VEC> rp;
         if (prev) {
           rp = ldp<Real, VEC>(prev + io);
         } else {
 #pragma unroll
           for (int kk = 0; kk < VEC; ++kk) rp.v[kk] = Real(0);
         }
-        const Real mi = m.minv[i];
         Real vi[VEC], acc[VEC];
 #pragma unroll
         for (int kk = 0; kk < VEC; ++kk) {
           vi[kk] = iP ? s_cur * rc.v[kk] : Real(0);
           acc[kk] = Real(0);
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int kk = 0; kk < VEC; ++kk) acc[kk] = fma(w[q].v[kk], s_cur * rj[q].v[kk] - vi[kk], acc[kk]);
-        for (int t = t0; t < t1; ++t) {  // neighbours beyond the fourth (rare)
-          const int2 on = m.adj[t];
-          const bool jP = on.x < nP;
-          if (!jP && !iP) break;  // sorted: no P neighbour left
-          const Pack<Real, VEC> wo = ldp<Real, VEC>(W + (size_t)on.y * S + s0);
-          if (jP) {
-            const Pack<Real, VEC> ro = ldp<Real, VEC>(cur + (size_t)on.x * SL + o);
-#pragma unroll
-            for (int kk = 0; kk < VEC; ++kk) acc[kk] = fma(wo.v[kk], s_cur * ro.v[kk] - vi[kk], acc[kk]);
+        const int t1 = sptr[i + 1];
+        for (int t = sptr[i]; t < t1; ++t) {
+          const int jl = sj[t];
+          const Pack<Real, VEC> w = ldp<Real, VEC>(wsm + (size_t)t * SL + o);
+          Pack<Real, VEC> rj;
+          if (jl >= 0) {
+            rj = ldp<Real, VEC>(cur + (size_t)jl * SL + o);
           } else {
 #pragma unroll
-            for (int kk = 0; kk < VEC; ++kk) acc[kk] = fma(wo.v[kk], -vi[kk], acc[kk]);
+            for (int kk = 0; kk < VEC; ++kk) rj.v[kk] = Real(0);
           }
+#pragma unroll
+          for (int kk = 0; kk < VEC; ++kk) acc[kk] = fma(w.v[kk], s_cur * rj.v[kk] - vi[kk], acc[kk]);
         }
+        const Real mi = sminv[i];
         Pack<Real, VEC> rn;
 #pragma unroll
         for (int kk = 0; kk < VEC; ++kk)

@@ -49,6 +49,10 @@ struct MeshGPU {
   float* psi32 = nullptr;
   double* psi64 = nullptr;
   int* new2old = nullptr;
+  // coupling slots of R for the fused inner kernel (built on first use)
+  int* rptr = nullptr;
+  int2* rslot = nullptr;
+  int64_t n_rslots = -1;
   // autotuned (vec, shape code) per (S, precision, p)
   std::map<std::tuple<int64_t, int, int>, std::pair<int, int>> tuned;
   // L2 blocks of the inner loop per (S, precision, p), uploaded lists
@@ -361,15 +365,18 @@ Geo geometry_vec(const lflts_ctx* c, int64_t n, int64_t S, int vec, int cta_per_
 // shared memory): lanes per node SBf (draw slab SL = SBf vec) and dynamic
 // shared memory; smem = 0 when R does not fit.
 constexpr size_t kFusedSmemMax = 200 * 1024;
-inline void fused_plan(const lflts_ctx* c, int n_R, int64_t S, int vec, size_t rb, int& SBf, size_t& smem) {
+inline void fused_plan(const lflts_ctx* c, int n_R, int64_t n_slots, int64_t S, int vec, size_t rb, int& SBf,
+                       size_t& smem) {
   (void)c;
   SBf = 1;
   smem = 0;
-  if (n_R < 1) return;
+  if (n_R < 1 || n_slots < 0) return;
   // lanes per node: fill the 256 threads of a CTA when R is small (the
   // kernels of a step are short; fewer, fuller CTAs load less index data)
   while (SBf < 8 && int64_t(n_R) * SBf * 2 <= 256 && int64_t(SBf) * 2 * vec <= S) SBf *= 2;
-  const size_t need = 4 * size_t(n_R) * size_t(SBf) * size_t(vec) * rb;
+  const int SL = SBf * vec;
+  const size_t need = (fused_real_count(n_R, static_cast<int>(n_slots), SL) * rb + 15) / 16 * 16 +
+                      (size_t(n_slots) + size_t(n_R) + 1) * sizeof(int);
   if (need <= kFusedSmemMax) smem = need;
 }
 
@@ -438,7 +445,7 @@ struct Stepper {
     coarse_bytes = Srb * (4.0 * h.n_free - 2.0 * n_R + double(h.n_edges));
     edgeP_bytes = Srb * double(h.n_edges_P);
     if (shape >= 2000 && n_R > 0 && p > 1 && p <= 64) {
-      fused_plan(c, n_R, S, VEC, sizeof(Real), fSB, fsmem);
+      fused_plan(c, n_R, mg.n_rslots, S, VEC, sizeof(Real), fSB, fsmem);
       fused = fsmem > 0;
       const int64_t SL = int64_t(fSB) * VEC;
       fgrid = static_cast<int>((S + SL - 1) / SL);
@@ -558,12 +565,13 @@ struct Stepper {
     if (n_R > 0 && blk) return inner_blocked(uc, un, d, kappa, st);
     if (n_R > 0 && fused) {
       Prof pr(c, st);
+      const int ns = static_cast<int>(mgp->n_rslots);
       if (dts)
         k_inner_fused<Real, VEC, true><<<fgrid, 256, fsmem, st>>>(md, (int)S, fSB, W, g, uc, un, d, coef, kappa,
-                                                                  (int)S_act);
+                                                                  (int)S_act, mgp->rptr, mgp->rslot, ns);
       else
         k_inner_fused<Real, VEC, false><<<fgrid, 256, fsmem, st>>>(md, (int)S, fSB, W, g, uc, un, d, coef, kappa,
-                                                                   (int)S_act);
+                                                                   (int)S_act, mgp->rptr, mgp->rslot, ns);
       LF_CUDA(c, cudaGetLastError());
       // g, u and d in, d and u out on R, the P-edge weights: once per step
       pr.end(LFLTS_KERNEL_INNER, 5.0 * n_R * Srb + edgeP_bytes);
@@ -685,11 +693,21 @@ int time_loop_vec(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, i
 // Whether the fused inner kernel can run this batch; raises its dynamic
 // shared-memory limit once it can (outside any graph capture).
 template <typename Real>
-bool fused_ok(lflts_ctx* c, int n_R, int64_t S, int vec, int p) {
+bool fused_ok(lflts_ctx* c, MeshGPU& mg, int n_R, int64_t S, int vec, int p) {
   if (n_R < 1 || p < 2 || p > 64) return false;
+  if (mg.n_rslots < 0) {  // coupling slots of R, built and uploaded once per mesh
+    std::vector<int32_t> ptr, sj, se;
+    build_r_slots(mg.h, ptr, sj, se);
+    if (int64_t(sj.size()) > (int64_t(1) << 24)) return false;
+    std::vector<int2> sl(sj.size());
+    for (size_t t = 0; t < sj.size(); ++t) sl[t] = make_int2(sj[t], se[t]);
+    if (upload(c, &mg.rptr, ptr.data(), ptr.size())) return false;
+    if (upload(c, &mg.rslot, sl.data(), sl.size())) return false;
+    mg.n_rslots = static_cast<int64_t>(sj.size());
+  }
   int SBf = 1;
   size_t smem = 0;
-  fused_plan(c, n_R, S, vec, sizeof(Real), SBf, smem);
+  fused_plan(c, n_R, mg.n_rslots, S, vec, sizeof(Real), SBf, smem);
   if (smem == 0) return false;
   cudaError_t e = cudaSuccess;
   const int mx = int(kFusedSmemMax);
@@ -827,7 +845,7 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
     if (S % v == 0) vecs.push_back(v);
   vec = vecs.front();
   cps = 16;
-  if (c->fused_mode == 2 && !blocks && fused_ok<Real>(c, n_R, S, vec, ds.p)) {
+  if (c->fused_mode == 2 && !blocks && fused_ok<Real>(c, mg, n_R, S, vec, ds.p)) {
     cps = 2016;
     return 0;
   }
@@ -854,7 +872,7 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
     // launch count per step outweighs the DRAM bytes it saves).  The fused
     // inner kernel is, where R fits in shared memory.
     std::vector<int> shapes = {8, 16, 32, 108, 116, 132};
-    if (c->fused_mode >= 1 && !blocks && fused_ok<Real>(c, n_R, S, v, ds.p))
+    if (c->fused_mode >= 1 && !blocks && fused_ok<Real>(c, mg, n_R, S, v, ds.p))
       for (int k : {8, 16, 32, 108, 116, 132}) shapes.push_back(2000 + k);
     for (int k : shapes) {
       Real* uc = nullptr;

@@ -236,6 +236,34 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
   return 0;
 }
 
+void build_r_slots(const HostMesh& m, std::vector<int32_t>& ptr, std::vector<int32_t>& slot_j,
+                   std::vector<int32_t>& slot_e) {
+  const int64_t nR = m.n_R, nP = m.n_P;
+  ptr.assign(1, 0);
+  slot_j.clear();
+  slot_e.clear();
+  for (int64_t i = 0; i < nR; ++i) {
+    const bool iP = i < nP;
+    for (int q = 0; q < 4; ++q) {
+      const int32_t j = m.ell_j[4 * i + q];
+      if (j < 0) continue;
+      const bool jP = j < nP;
+      if (jP || iP) {
+        slot_j.push_back(jP ? j : -1);
+        slot_e.push_back(m.ell_e[4 * i + q]);
+      }
+    }
+    for (int32_t t = m.adj_ptr[i] + 4; t < m.adj_ptr[i + 1]; ++t) {
+      const int32_t j = m.adj_j[t];
+      const bool jP = j < nP;
+      if (!jP && !iP) break;  // sorted: no P neighbour left
+      slot_j.push_back(jP ? j : -1);
+      slot_e.push_back(m.adj_e[t]);
+    }
+    ptr.push_back(static_cast<int32_t>(slot_j.size()));
+  }
+}
+
 void build_inner_blocks(const HostMesh& m, int p, int64_t core, InnerBlocks& out) {
   const int64_t nR = m.n_R, nP = m.n_P;
   out.nodes.clear();

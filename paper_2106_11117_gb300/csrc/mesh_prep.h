@@ -64,6 +64,15 @@ struct InnerBlocks {
 // order of the node coordinates) and attach p-2 halo layers.
 void build_inner_blocks(const HostMesh& m, int p, int64_t core, InnerBlocks& out);
 
+// Coupling slots of the inner substeps on R, in the order the per-substep
+// kernel visits them (the four table entries, then the rest of the
+// adjacency list), without the slots that add nothing: node i < n_R keeps
+// neighbour j when j is in P (r_j enters a(P r)_i) or i is in P (w_ij r_i
+// enters).  slot_j = j for j in P, else -1; slot_e = edge id.  ptr has
+// n_R + 1 offsets.
+void build_r_slots(const HostMesh& m, std::vector<int32_t>& ptr, std::vector<int32_t>& slot_j,
+                   std::vector<int32_t>& slot_e);
+
 // Returns 0 on success; on failure fills err and returns a negative status.
 int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
               const uint8_t* dirichlet, const uint8_t* P, const double* psi, int K,
