@@ -82,10 +82,11 @@ enum {
                              bit for bit, fewer DRAM bytes, more launches); 0 (default): one launch
                              per substep over R */
   LFLTS_OPT_BLOCK_BUDGET = 4, /* bytes of inner-loop working set per L2 block (default 40e6) */
-  LFLTS_OPT_FUSED_INNER = 5   /* all p-1 inner substeps of a step in one launch, R and the draws of a
-                                 CTA in shared memory (only where 4 |R| x slab values fit in 200 KB;
-                                 same results bit for bit): 0 never, 1 (default) when the autotuner
-                                 measures it faster, 2 always where it fits */
+  LFLTS_OPT_FUSED_INNER = 5   /* all p-1 inner substeps of a step in one launch, with R's recursion,
+                                 coupling slots, their edge weights and 1/m for a CTA's draws in
+                                 shared memory (only where they fit in 200 KB; same results bit for
+                                 bit): 0 never; 1 (default) autotuned, and always where it fits and
+                                 |R| <= 2048; 2 always where it fits */
 };
 
 /* Library version (major*10000 + minor*100 + patch). */

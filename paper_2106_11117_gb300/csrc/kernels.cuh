@@ -41,6 +41,7 @@ struct MeshDev {
   const int2* __restrict__ adj;      // (neighbour, edge), sorted by neighbour
   const int4* __restrict__ ell;      // [n_free][2]: first four (neighbour, edge), neighbour -1 = empty
   const Real* __restrict__ minv;     // [n_free]
+  const int4* __restrict__ ell_hi;   // [n_free][2]: entries 5..8, or null (meshes of degree about 4)
 };
 
 // The first four neighbours of node i (almost every node of the meshes has
@@ -49,8 +50,9 @@ struct Nb4 {
   int j[4], e[4];
 };
 template <typename Real>
-__device__ __forceinline__ Nb4 load_nb4(const MeshDev<Real>& m, int i) {
-  const int4 a = __ldg(m.ell + 2 * i), b = __ldg(m.ell + 2 * i + 1);
+__device__ __forceinline__ Nb4 load_nb4(const MeshDev<Real>& m, int i, bool hi = false) {
+  const int4* tab = hi ? m.ell_hi : m.ell;
+  const int4 a = __ldg(tab + 2 * i), b = __ldg(tab + 2 * i + 1);
   Nb4 r;
   r.j[0] = a.x; r.e[0] = a.y; r.j[1] = a.z; r.e[1] = a.w;
   r.j[2] = b.x; r.e[2] = b.y; r.j[3] = b.z; r.e[3] = b.w;
@@ -184,7 +186,9 @@ k_edge_weights(int64_t n_edges, int S, int SB, const int2* __restrict__ ee,
 // ---------------------------------------------------------------------------
 // RAG: a ragged batch (draws [S_lim, S) finished: their u and d are not
 // written; per-draw forcing amplitude); otherwise S_lim and rf are unused.
-template <typename Real, int VEC, int MINB = 1, bool RAG = false>
+// HI: the mesh has the table of entries 5..8 (general triangulations); the
+// neighbours are summed in the same order either way.
+template <typename Real, int VEC, int MINB = 1, bool RAG = false, bool HI = false>
 __global__ void __launch_bounds__(256, MINB)
 k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real* __restrict__ u,
          Real* __restrict__ u_next, Real* __restrict__ d, Real* __restrict__ g, Real kappa_gamma,
@@ -199,7 +203,9 @@ k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real*
     const bool outside = i >= m.n_R;
     // issue every independent load of this node before any arithmetic
     const Nb4 nb = load_nb4(m, i);
-    const int t0 = m.adj_ptr[i] + 4, t1 = m.adj_ptr[i + 1];
+    Nb4 nb2;
+    if constexpr (HI) nb2 = load_nb4(m, i, true);
+    const int t0 = m.adj_ptr[i] + (HI ? 8 : 4), t1 = m.adj_ptr[i + 1];
     const Pack<Real, VEC> ui = ldp<Real, VEC>(u + is);
     Pack<Real, VEC> uj[4], w[4], dn;
 #pragma unroll
@@ -221,7 +227,21 @@ k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real*
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int k = 0; k < VEC; ++k) acc[k] = fma(w[q].v[k], uj[q].v[k] - ui.v[k], acc[k]);
-    for (int t = t0; t < t1; ++t) {  // neighbours beyond the fourth (rare)
+    if constexpr (HI) {  // neighbours 5..8: indices already loaded
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (nb2.j[q] >= 0) {
+          uj[q] = ldp<Real, VEC>(u + (size_t)nb2.j[q] * S + s0);
+          w[q] = ldp<Real, VEC>(W + (size_t)nb2.e[q] * S + s0);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (nb2.j[q] >= 0)
+#pragma unroll
+          for (int k = 0; k < VEC; ++k) acc[k] = fma(w[q].v[k], uj[q].v[k] - ui.v[k], acc[k]);
+    }
+    for (int t = t0; t < t1; ++t) {  // neighbours beyond the fourth (eighth with HI)
       const int2 o = m.adj[t];
       const Pack<Real, VEC> uo = ldp<Real, VEC>(u + (size_t)o.x * S + s0);
       const Pack<Real, VEC> wo = ldp<Real, VEC>(W + (size_t)o.y * S + s0);

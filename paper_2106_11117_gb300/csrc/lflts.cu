@@ -40,6 +40,7 @@ struct MeshGPU {
   int* adj_ptr = nullptr;
   int2* adj = nullptr;
   int4* ell = nullptr;
+  int4* ell_hi = nullptr;   // entries 5..8 (general triangulations) or null
   int2* ee = nullptr;       // elements of each edge
   int2* ends = nullptr;     // endpoints of each edge (i < j)
   float* eg32 = nullptr;    // [n_edges][2] element entries G
@@ -338,7 +339,7 @@ struct Sel;
 template <>
 struct Sel<float> {
   static MeshDev<float> mesh(const MeshGPU& m, int n_R) {
-    return MeshDev<float>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.adj_ptr, m.adj, m.ell, m.minv32};
+    return MeshDev<float>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.adj_ptr, m.adj, m.ell, m.minv32, m.ell_hi};
   }
   static const float* field(const Field& f) { return f.v32; }
   static const float* eg(const MeshGPU& m) { return m.eg32; }
@@ -348,7 +349,7 @@ struct Sel<float> {
 template <>
 struct Sel<double> {
   static MeshDev<double> mesh(const MeshGPU& m, int n_R) {
-    return MeshDev<double>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.adj_ptr, m.adj, m.ell, m.minv64};
+    return MeshDev<double>{(int)m.h.n_free, n_R, (int)m.h.n_P, m.adj_ptr, m.adj, m.ell, m.minv64, m.ell_hi};
   }
   static const double* field(const Field& f) { return f.v64; }
   static const double* eg(const MeshGPU& m) { return m.eg64; }
@@ -549,15 +550,20 @@ struct Stepper {
       const Real kg = (Real)(double(kappa) * gamma);
       const Real fa = source_amp(double(n) * dt);
       const RaggedF rf = ragged(n);
-#define LF_COARSE(B, RG) \
-  k_coarse<Real, VEC, B, RG><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg, fw, fa, (int)S_act, rf)
+#define LF_COARSE(B, RG, HI)                                                                              \
+  k_coarse<Real, VEC, B, RG, HI><<<gc.grid, 256, 0, st>>>(md, (int)S, gc.SB, W, uc, un, d, g, kg, fw, fa, (int)S_act, \
+                                                          rf)
+#define LF_COARSE_H(B, RG)         \
+  if (md.ell_hi) LF_COARSE(B, RG, true); \
+  else LF_COARSE(B, RG, false)
       if (dts) {  // ragged batch (bounded to 64 registers: four CTAs of 256 per SM)
-        if (minb6) LF_COARSE(6, true);
-        else LF_COARSE(4, true);
+        if (minb6) LF_COARSE_H(6, true);
+        else LF_COARSE_H(4, true);
       } else {
-        if (minb6) LF_COARSE(6, false);
-        else LF_COARSE(1, false);
+        if (minb6) LF_COARSE_H(6, false);
+        else LF_COARSE_H(1, false);
       }
+#undef LF_COARSE_H
 #undef LF_COARSE
       LF_CUDA(c, cudaGetLastError());
       pr.end(LFLTS_KERNEL_COARSE, coarse_bytes);
@@ -871,9 +877,14 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
     // 10-35 % slower than one launch per substep at the benchmark shapes (the
     // launch count per step outweighs the DRAM bytes it saves).  The fused
     // inner kernel is, where R fits in shared memory.
+    // For a small R (at most 2048 nodes) the fused kernel replaces p-1
+    // launches of a few microseconds each; a four-step timing does not tell
+    // the two apart reliably there, so only the fused shapes are timed.
     std::vector<int> shapes = {8, 16, 32, 108, 116, 132};
-    if (c->fused_mode >= 1 && !blocks && fused_ok<Real>(c, mg, n_R, S, v, ds.p))
+    if (c->fused_mode >= 1 && !blocks && fused_ok<Real>(c, mg, n_R, S, v, ds.p)) {
+      if (n_R <= 2048) shapes.clear();
       for (int k : {8, 16, 32, 108, 116, 132}) shapes.push_back(2000 + k);
+    }
     for (int k : shapes) {
       Real* uc = nullptr;
       int rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, 1, blocks, dts);  // warm
@@ -1525,6 +1536,13 @@ int lflts_mesh_add(lflts_ctx* c, const double* xy, int64_t n_nodes, const int32_
         ell[2 * i + hh] = make_int4(h.ell_j[4 * i + 2 * hh], h.ell_e[4 * i + 2 * hh], h.ell_j[4 * i + 2 * hh + 1],
                                     h.ell_e[4 * i + 2 * hh + 1]);
     LF_TRY(upload(c, &mg->ell, ell.data(), ell.size()));
+    if (!h.ell_hi_j.empty()) {
+      for (int64_t i = 0; i < h.n_free; ++i)
+        for (int hh = 0; hh < 2; ++hh)
+          ell[2 * i + hh] = make_int4(h.ell_hi_j[4 * i + 2 * hh], h.ell_hi_e[4 * i + 2 * hh],
+                                      h.ell_hi_j[4 * i + 2 * hh + 1], h.ell_hi_e[4 * i + 2 * hh + 1]);
+      LF_TRY(upload(c, &mg->ell_hi, ell.data(), ell.size()));
+    }
     LF_TRY(upload(c, &mg->ee, ee.data(), ne));
     std::vector<int2> ends(ne);
     for (size_t k = 0; k < ne; ++k) ends[k] = make_int2(h.edge_i[k], h.edge_j[k]);

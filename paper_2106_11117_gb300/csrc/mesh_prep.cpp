@@ -233,6 +233,21 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
       }
     }
   }
+  // entries 5..8 in a second table where many nodes have more than four
+  // neighbours (general triangulations: about six)
+  int64_t wide = 0;
+  for (int64_t i = 0; i < m.n_free; ++i) wide += (m.adj_ptr[i + 1] - m.adj_ptr[i]) > 4;
+  m.ell_hi_j.clear();
+  m.ell_hi_e.clear();
+  if (m.n_free > 0 && 4 * wide >= m.n_free) {
+    m.ell_hi_j.assign(static_cast<size_t>(m.n_free) * 4, -1);
+    m.ell_hi_e.assign(static_cast<size_t>(m.n_free) * 4, 0);
+    for (int64_t i = 0; i < m.n_free; ++i)
+      for (int32_t t = m.adj_ptr[i] + 4; t < std::min(m.adj_ptr[i] + 8, m.adj_ptr[i + 1]); ++t) {
+        m.ell_hi_j[4 * i + (t - m.adj_ptr[i] - 4)] = m.adj_j[t];
+        m.ell_hi_e[4 * i + (t - m.adj_ptr[i] - 4)] = m.adj_e[t];
+      }
+  }
   return 0;
 }
 

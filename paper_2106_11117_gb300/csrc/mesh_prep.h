@@ -39,6 +39,10 @@ struct HostMesh {
   // table [n_free][4] (neighbour, edge), padded with neighbour -1; entries
   // beyond the fourth stay in adj_j/adj_e from adj_ptr[i] + 4 on.
   std::vector<int32_t> ell_j, ell_e;
+  // Entries 5..8 in a second table of the same shape, built only when at
+  // least a quarter of the free nodes have more than four neighbours (empty
+  // otherwise); entries beyond the eighth then start at adj_ptr[i] + 8.
+  std::vector<int32_t> ell_hi_j, ell_hi_e;
   std::vector<int32_t> edge_i, edge_j;     // endpoints (new ids), edge_i < edge_j
   std::vector<int32_t> edge_e0, edge_e1;   // element ids (new order), e1 = -1 on the boundary
   std::vector<double> edge_G0, edge_G1;    // G_e0[i][j], G_e1[i][j] (0 when e1 = -1)
