@@ -217,10 +217,18 @@ int lflts_level_sums(lflts_ctx* ctx, const double* Qf, const double* Qc,
  * One MLMC level pair (Alg. 1 step 2a): Q_l and Q_{l-1} of the same draws
  * (the coarse solve is skipped when has_coarse == 0, level 0), the
  * differences dQ and the level sums.  Solves that share mesh, QoI, fields,
- * precision, p, nu, dt and n_steps across the jobs of one call are merged
- * into a single batched solve.  Independent solves run concurrently on
- * streams of the context, joined back into `stream`.
+ * precision, p, nu and source across the jobs of one call are merged into a
+ * single batched solve; when their (dt, n_steps) differ (draws with their
+ * own time step, e.g. from a per-draw CFL bound) the batch is ragged: every
+ * draw steps with its own dt for its own count and its QoI is taken at its
+ * own final time (results equal those of separate batches to rounding).
+ * Independent batches run concurrently on streams of the context, joined
+ * back into `stream`.
  *   xi [S][K]; dQ, Qf [S] (Qf may be NULL); sums [4] (may be NULL).
+ * Errors: LFLTS_ERR_ARG for a bad job (null xi or dQ, S < 1, a descriptor
+ * that lflts_solve would refuse, fine and coarse meshes with different K,
+ * a merged batch above 2,097,120 draws); LFLTS_ERR_UNSTABLE (host mode only)
+ * for a non-finite QoI.
  */
 typedef struct {
   lflts_solve_desc fine;
