@@ -247,8 +247,8 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     cfg = _cfg(args.config)
-    pool = None
-    if rank == 0 and not args.no_cpu_baseline:
+    pool = None  # the CPU baseline runs at N = 1 only (rank 0 of one process)
+    if world == 1 and not args.no_cpu_baseline:
         pool = OraclePool(args.cpu_cores or os.cpu_count() or 1)
     W = setup_gpu(cfg, rank)
     lf = W["lflts"]
@@ -331,7 +331,7 @@ def run_ours(args):
             "share_of_kernel_time": round(pd["ms"] / sum(v["ms"] for v in prof.values()), 4)}
 
     tte = None
-    if rank == 0 and not args.no_time_to_eps:
+    if world == 1 and not args.no_time_to_eps:
         tte = time_to_eps(args.eps)
 
     cpu = None

@@ -36,6 +36,23 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(lib.EXPORTED) == set(declared)
 
 
+def test_binding_constants_match_header(lib):
+    """Status codes, memory kinds, options and kernel classes of the Python
+    binding carry the values the header's enums give them."""
+    src = open(os.path.join(ROOT, "include", "lflts.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    enum = {k: int(v) for k, v in re.findall(r"\b(LFLTS_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    for name, value in enum.items():
+        if name.startswith("LFLTS_KERNEL_"):
+            cls = name[len("LFLTS_KERNEL_"):].lower()
+            if cls != "classes":
+                assert lib.KERNEL_CLASSES[cls] == value, name
+        else:
+            assert getattr(lib, name) == value, name
+    assert len(lib.KERNEL_CLASSES) == enum["LFLTS_KERNEL_CLASSES"]
+    assert enum["LFLTS_OPT_FUSED_INNER"] == 5 and enum["LFLTS_KERNEL_ADJ_EDGES"] == 6
+
+
 @pytest.mark.parametrize("p,nu", [(1, 0.0), (2, 0.01), (4, 0.01), (8, 0.5), (16, 0.01)])
 def test_library_constants_match_oracle(lib, p, nu):
     from oracle.lts import lts_constants
