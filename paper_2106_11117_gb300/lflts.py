@@ -71,6 +71,10 @@ class SolveDesc(C.Structure):
 
 
 class PairJob(C.Structure):
+    """lflts_pair_job: raw pointers (numpy ``ctypes.data`` or torch
+    ``data_ptr()``), so every array a job points to must stay alive until
+    lflts_run_pairs has returned (host buffers) or its stream has finished
+    (device buffers)."""
     _fields_ = [("fine", SolveDesc), ("coarse", SolveDesc), ("has_coarse", C.c_int),
                 ("xi", C.c_void_p), ("S", C.c_int64), ("dQ", C.c_void_p), ("Qf", C.c_void_p),
                 ("sums", C.c_void_p)]

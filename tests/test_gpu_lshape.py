@@ -50,10 +50,10 @@ def test_lshape_buckets_match_oracle(lf, precision, tol):
                 j.xi, j.S = x.ctypes.data, len(sel)
                 j.dQ, j.Qf, j.sums = dQ.ctypes.data, Qf.ctypes.data, sums.ctypes.data
                 jobs.append(j)
-                meta.append((l, key, x, dQ, Qf))
+                meta.append((l, key, x, dQ, Qf, sums))  # the jobs point into these arrays
         assert len(jobs) > 2  # uneven: several buckets per level pair
         lf.lflts_run_pairs(ctx.h, jobs)
-        for l, (kf, kc), x, dQ, Qf in meta:
+        for l, (kf, kc), x, dQ, Qf, _ in meta:
             for i in range(min(3, x.shape[0])):
                 qf = solve_qoi(dict(levs[l], dt=levs[l]["T"] / kf, n_steps=kf), x[i])
                 qc = solve_qoi(dict(levs[l - 1], dt=levs[l - 1]["T"] / kc, n_steps=kc), x[i])

@@ -30,6 +30,10 @@ def _level_with_source(p):
     return dict(lev, source={"nodes": nodes, "weights": w, "f0": 6.0, "t0": 0.2, "amp": 2.0})
 
 
+# The jobs hold raw pointers: every array they point to must outlive the call.
+_ALIVE = []
+
+
 def _job(lf, h, prec, dt, n, x, outs):
     j = lf.PairJob()
     j.fine = h.desc(prec)
@@ -37,6 +41,7 @@ def _job(lf, h, prec, dt, n, x, outs):
     j.xi, j.S = x.ctypes.data, x.shape[0]
     dQ, Qf, sums = np.zeros(x.shape[0]), np.zeros(x.shape[0]), np.zeros(4)
     j.dQ, j.Qf, j.sums = dQ.ctypes.data, Qf.ctypes.data, sums.ctypes.data
+    _ALIVE.append((x, dQ, sums))
     outs.append(Qf)
     return j
 
