@@ -1,9 +1,12 @@
 // C ABI of the LF-LTS / MLMC library (declared in include/lflts.h).
 //
-// Host orchestration of the kernels in kernels.cuh: mesh upload, per-solve
-// workspaces, the time loop of Alg. 2 (one coarse launch and p-1 inner
-// launches per step), the QoI reduction and the MLMC level sums, merged
-// batched solves for level pairs, profiling counters.
+// Host orchestration of the kernels in kernels.cuh and adjoint.cuh: mesh
+// upload, per-solve workspaces, the time loop of Alg. 2 (one coarse launch
+// and p-1 inner launches per step, or one fused inner launch for a small R),
+// the QoI reduction and the MLMC level sums, merged batched solves for level
+// pairs (ragged batches for draws with their own time steps, long solves
+// queued in slices across streams), CUDA graphs, the launch-shape autotuner,
+// the discrete adjoint and profiling counters.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -625,7 +628,8 @@ struct Stepper {
   }
 };
 
-// The time loop of Alg. 2 for one batch.
+// A few steps of Alg. 2 for one batch with a given launch shape (the
+// autotuner's timing runs; solves run through SlicedLoop).
 template <typename Real, int VEC>
 int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S,
               Workspace& ws, Real*& uc_out, cudaStream_t st, int cta_per_sm = 16, int64_t n_steps = -1,
@@ -838,10 +842,12 @@ std::unique_ptr<SliceTask> make_sliced(lflts_ctx* c, const lflts_solve_desc& ds,
 }
 
 // Launch shape of the step kernels for a batch: draws per thread (vec),
-// CTAs per SM and the register cap (shape code cps: CTAs per SM, +100 for the
-// instantiation limited to 40 registers so that 6 CTAs of 256 fit an SM).  With autotuning on, the first solve of a (mesh, S,
-// precision, p) times every candidate over a few steps on the real buffers
-// (the state is re-initialised afterwards) and keeps the fastest.
+// CTAs per SM and the register cap.  Shape code cps: CTAs per SM, +100 for
+// the instantiation limited to 40 registers (6 CTAs of 256 per SM), +1000
+// for the L2-blocked inner loop (opt-in only), +2000 for the fused inner
+// kernel.  With autotuning on, the first solve of a (mesh, S, precision, p)
+// times every candidate over a few steps on the real buffers (the state is
+// re-initialised afterwards) and keeps the fastest.
 template <typename Real>
 int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
                  cudaStream_t st, int& vec, int& cps, const MeshGPU::DevBlocks* blocks, const double* dts) {
