@@ -15,4 +15,7 @@ Modules
         optimal_Nl, bias_est, Alg. 1)
   adjoint  discrete adjoint of the u-form LF-LTS solve with full history
         and central finite differences (gradient of Q with respect to xi)
+  field_qoi  the L2(D)-valued QoI u(., T) (Sec. 4): interpolation between
+        level meshes, the consistent mass matrix, V-norm level sums, mean and
+        variance (Eqs. MLMCestimator, Vell_est, bias_est in V = L2(D))
 """
