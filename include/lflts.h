@@ -152,6 +152,23 @@ int lflts_mesh_order(lflts_ctx* ctx, int mesh_id, int32_t* new2old);
 int lflts_lts_constants(int p, double nu, double dt, double* out);
 
 /*
+ * Nodal interpolation between two meshes of one domain (host only; no
+ * context or device): for every node k of the fine mesh, xy_f[2k..2k+1]
+ * (caller's numbering), the vertices vert[3k..3k+2] of a triangle of the
+ * coarse mesh (xy_c [n_c][2], tri_c [n_tri_c][3], caller's numbering) that
+ * contains it and its barycentric coordinates w[3k..3k+2] (they sum to 1),
+ * so that the coarse P1 function u_c takes the value
+ * sum_a w[3k+a] u_c[vert[3k+a]] there.  This forms dQ_l = u_l - I u_{l-1}
+ * of the L2(D)-valued QoI u(., T) (Sec. 4) on the finer mesh of a pair.
+ * Caller-owned buffers: vert [n_f][3] int32, w [n_f][3] FP64.
+ * Errors: LFLTS_ERR_ARG for null pointers, sizes below 1 or vertex ids
+ * outside [0, n_c); LFLTS_ERR_MESH if some fine node lies outside every
+ * coarse triangle (a barycentric coordinate below -1e-10).
+ */
+int lflts_interp_weights(const double* xy_c, int64_t n_c, const int32_t* tri_c, int64_t n_tri_c,
+                         const double* xy_f, int64_t n_f, int32_t* vert, double* w);
+
+/*
  * Register a nodal field (initial displacement u0 or velocity v0, Sec. 2.1)
  * on a mesh: values [n_nodes] FP64 in the caller's node order; values on
  * Dirichlet nodes are replaced by 0.

@@ -1589,6 +1589,15 @@ int lflts_mesh_order(lflts_ctx* c, int mesh_id, int32_t* new2old) {
   return LFLTS_OK;
 }
 
+int lflts_interp_weights(const double* xy_c, int64_t n_c, const int32_t* tri_c, int64_t n_tri_c,
+                         const double* xy_f, int64_t n_f, int32_t* vert, double* w) {
+  if (!xy_c || !tri_c || !xy_f || !vert || !w || n_c < 3 || n_tri_c < 1 || n_f < 1) return LFLTS_ERR_ARG;
+  for (int64_t k = 0; k < 3 * n_tri_c; ++k)
+    if (tri_c[k] < 0 || tri_c[k] >= n_c) return LFLTS_ERR_ARG;
+  const int64_t outside = interp_weights(xy_c, tri_c, n_tri_c, xy_f, n_f, vert, w, 1e-10);
+  return outside ? LFLTS_ERR_MESH : LFLTS_OK;
+}
+
 int lflts_lts_constants(int p, double nu, double dt, double* out) {
   if (!out || p < 1 || p > 64 || !(nu >= 0.0 && nu <= 1.0) || !(dt > 0.0)) return LFLTS_ERR_ARG;
   std::vector<double> beta, cm;

@@ -251,6 +251,77 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
   return 0;
 }
 
+int64_t interp_weights(const double* xy_c, const int32_t* tri_c, int64_t n_tri_c, const double* xy_f,
+                       int64_t n_f, int32_t* vert, double* w, double tol) {
+  if (n_tri_c < 1 || n_f < 1) return n_f;
+  double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+  for (int64_t t = 0; t < n_tri_c; ++t)
+    for (int a = 0; a < 3; ++a) {
+      const double* p = xy_c + 2 * int64_t(tri_c[3 * t + a]);
+      x0 = std::min(x0, p[0]);
+      x1 = std::max(x1, p[0]);
+      y0 = std::min(y0, p[1]);
+      y1 = std::max(y1, p[1]);
+    }
+  const int64_t G = std::max<int64_t>(1, static_cast<int64_t>(std::sqrt(double(n_tri_c))));
+  const double sx = double(G) / std::max(x1 - x0, 1e-300), sy = double(G) / std::max(y1 - y0, 1e-300);
+  auto cell = [&](double v, double lo, double sc) {
+    return std::min<int64_t>(G - 1, std::max<int64_t>(0, static_cast<int64_t>((v - lo) * sc)));
+  };
+  // buckets: triangles whose bounding box meets the cell (CSR)
+  std::vector<int64_t> count(size_t(G * G) + 1, 0);
+  auto for_cells = [&](int64_t t, auto&& fn) {
+    double a0 = 1e300, a1 = -1e300, b0 = 1e300, b1 = -1e300;
+    for (int a = 0; a < 3; ++a) {
+      const double* p = xy_c + 2 * int64_t(tri_c[3 * t + a]);
+      a0 = std::min(a0, p[0]);
+      a1 = std::max(a1, p[0]);
+      b0 = std::min(b0, p[1]);
+      b1 = std::max(b1, p[1]);
+    }
+    for (int64_t j = cell(b0, y0, sy); j <= cell(b1, y0, sy); ++j)
+      for (int64_t i = cell(a0, x0, sx); i <= cell(a1, x0, sx); ++i) fn(j * G + i);
+  };
+  for (int64_t t = 0; t < n_tri_c; ++t) for_cells(t, [&](int64_t c) { ++count[size_t(c) + 1]; });
+  for (size_t c = 0; c < size_t(G * G); ++c) count[c + 1] += count[c];
+  std::vector<int32_t> items(size_t(count.back()));
+  std::vector<int64_t> fill(count.begin(), count.end() - 1);
+  for (int64_t t = 0; t < n_tri_c; ++t)
+    for_cells(t, [&](int64_t c) { items[size_t(fill[size_t(c)]++)] = static_cast<int32_t>(t); });
+  int64_t outside = 0;
+  for (int64_t k = 0; k < n_f; ++k) {
+    const double px = xy_f[2 * k], py = xy_f[2 * k + 1];
+    const int64_t c = cell(py, y0, sy) * G + cell(px, x0, sx);
+    double best = -1e300, bl[3] = {0, 0, 0};
+    int64_t bt = -1;
+    for (int64_t q = count[size_t(c)]; q < count[size_t(c) + 1]; ++q) {
+      const int64_t t = items[size_t(q)];
+      const double* p0 = xy_c + 2 * int64_t(tri_c[3 * t]);
+      const double* p1 = xy_c + 2 * int64_t(tri_c[3 * t + 1]);
+      const double* p2 = xy_c + 2 * int64_t(tri_c[3 * t + 2]);
+      const double e1x = p1[0] - p0[0], e1y = p1[1] - p0[1], e2x = p2[0] - p0[0], e2y = p2[1] - p0[1];
+      const double det = e1x * e2y - e1y * e2x;
+      if (det == 0.0) continue;
+      const double dx = px - p0[0], dy = py - p0[1];
+      const double l1 = (dx * e2y - dy * e2x) / det, l2 = (e1x * dy - e1y * dx) / det, l0 = 1.0 - l1 - l2;
+      const double worst = std::min(l0, std::min(l1, l2));
+      if (worst > best) {
+        best = worst;
+        bt = t;
+        bl[0] = l0;
+        bl[1] = l1;
+        bl[2] = l2;
+      }
+    }
+    if (bt < 0 || best < -tol) ++outside;
+    for (int a = 0; a < 3; ++a) {
+      vert[3 * k + a] = bt < 0 ? 0 : tri_c[3 * bt + a];
+      w[3 * k + a] = bt < 0 ? 0.0 : bl[a];
+    }
+  }
+  return outside;
+}
+
 void build_r_slots(const HostMesh& m, std::vector<int32_t>& ptr, std::vector<int32_t>& slot_j,
                    std::vector<int32_t>& slot_e) {
   const int64_t nR = m.n_R, nP = m.n_P;

@@ -77,6 +77,16 @@ void build_inner_blocks(const HostMesh& m, int p, int64_t core, InnerBlocks& out
 void build_r_slots(const HostMesh& m, std::vector<int32_t>& ptr, std::vector<int32_t>& slot_j,
                    std::vector<int32_t>& slot_e);
 
+// Nodal interpolation between two triangulations of one domain: for every
+// point xy_f[k] the vertices vert[3k..3k+2] of a triangle of (xy_c, tri_c)
+// that contains it and the barycentric coordinates w[3k..3k+2].  Point
+// location through a uniform bucket grid over the triangles' bounding
+// boxes; among the candidates the triangle whose smallest coordinate is
+// largest is taken.  Returns the number of points outside every triangle
+// (smallest coordinate below -tol); their best candidate is still written.
+int64_t interp_weights(const double* xy_c, const int32_t* tri_c, int64_t n_tri_c, const double* xy_f,
+                       int64_t n_f, int32_t* vert, double* w, double tol);
+
 // Returns 0 on success; on failure fills err and returns a negative status.
 int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
               const uint8_t* dirichlet, const uint8_t* P, const double* psi, int K,

@@ -38,7 +38,7 @@ EXPORTED = [
     "lflts_qoi_add", "lflts_solve", "lflts_level_sums", "lflts_run_pairs",
     "lflts_profile_enable", "lflts_profile_reset", "lflts_profile_read", "lflts_launch_count",
     "lflts_qoi_reduce_noalloc", "lflts_grad_xi", "lflts_set_option", "lflts_get_stats",
-    "lflts_source_add",
+    "lflts_source_add", "lflts_interp_weights",
 ]
 LFLTS_OPT_GRAPHS = 1
 LFLTS_OPT_AUTOTUNE = 2
@@ -119,6 +119,7 @@ def load(path: str | None = None):
         "lflts_set_option": (i32, [vp, i32, i64]),
         "lflts_source_add": (i32, [vp, i32, vp, vp, i64, C.POINTER(i32)]),
         "lflts_get_stats": (i32, [vp, vp]),
+        "lflts_interp_weights": (i32, [vp, i64, vp, i64, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -199,6 +200,22 @@ def lflts_mesh_order(ctx, mesh_id):
     out = np.zeros(n, dtype=np.int32)
     _check(ctx, load().lflts_mesh_order(ctx, mesh_id, _ptr(out)))
     return out
+
+
+def lflts_interp_weights(xy_c, tri_c, xy_f):
+    """(vert [n_f, 3] int32, w [n_f, 3]): the coarse triangle's vertices and
+    barycentric coordinates at every fine node (host only)."""
+    xy_c = np.ascontiguousarray(xy_c, dtype=np.float64)
+    tri_c = np.ascontiguousarray(tri_c, dtype=np.int32)
+    xy_f = np.ascontiguousarray(xy_f, dtype=np.float64)
+    vert = np.zeros((xy_f.shape[0], 3), dtype=np.int32)
+    w = np.zeros((xy_f.shape[0], 3), dtype=np.float64)
+    rc = load().lflts_interp_weights(_ptr(xy_c), xy_c.shape[0], _ptr(tri_c), tri_c.shape[0], _ptr(xy_f),
+                                     xy_f.shape[0], _ptr(vert), _ptr(w))
+    if rc != LFLTS_OK:
+        raise LfltsError(rc, "interp_weights: " + ("a fine node lies outside the coarse mesh"
+                                                   if rc == LFLTS_ERR_MESH else "bad arguments"))
+    return vert, w
 
 
 def lflts_lts_constants(p, nu, dt):
