@@ -1,0 +1,48 @@
+"""Host-side pieces of bench.py (no GPU): the nvidia-smi clock summary that
+decides whether a bench line is valid (median SM clock, throttle reasons),
+the roofline record of a kernel class, and the oracle's work count."""
+import bench
+
+
+def test_clock_rows_median_max_and_reasons():
+    lines = [
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, 2055, 2070, 1350.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+        "0, 2070, 2070, 1390.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "garbage line\n",
+    ]
+    c = bench.parse_clock_rows(lines)
+    assert c["samples"] == 3
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    lines.append("0, 1800, 2070, 800.0, 0x0000000000000040, Not Active, Active, Not Active, Not Active\n")
+    c = bench.parse_clock_rows(lines)
+    assert c["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert bench.parse_clock_rows(["x\n"]) is None
+
+
+def test_roofline_record_of_the_dominant_class():
+    prof = {"coarse": {"launches": 10, "ms": 20.0, "alg_bytes": 100e9},
+            "inner": {"launches": 70, "ms": 60.0, "alg_bytes": 360e9},
+            "qoi": {"launches": 1, "ms": 0.1, "alg_bytes": 1e6}}
+    r = bench._roofline(prof, ("coarse", "inner"), {"coarse": "k_coarse", "inner": "k_inner"}, 1.05)
+    assert r["kernel"] == "k_inner"
+    assert r["achieved"] == round(360e9 / 0.060 / 1e9, 1)
+    assert r["frac"] == round(r["achieved"] / r["peak"], 4)
+    assert abs(r["traffic"] - 1.05 * 360e9 / 70) < 1.0
+    assert abs(r["share_of_kernel_time"] - round(60.0 / 80.1, 4)) < 1e-12
+    j = bench._classes_json(prof)
+    assert j["inner"]["alg_GBps"] == round(360e9 / 0.060 / 1e9, 1)
+
+
+def test_oracle_work_count_matches_the_metric():
+    """N_steps (n_free + p |R|) with R the vertices of elements touching P:
+    the unit of the benchmark's metric, counted on the host."""
+    cfg = bench._cfg("plain")
+    units = bench.oracle_units_per_sample(cfg, 0)
+    from workload import level_problem
+    lev = level_problem(cfg, 0)
+    m = lev["mesh"]
+    free = ~m.dirichlet.astype(bool)
+    assert units > lev["n_steps"] * int(free.sum())
+    assert units < lev["n_steps"] * (1 + cfg.p) * int(free.sum())
