@@ -93,10 +93,13 @@ enum {
 int lflts_version(void);
 
 /* Create a context on CUDA device `device` (or -1: a host-only context that
- * can prepare meshes but not solve).  *out receives the handle. */
+ * can prepare meshes but not solve).  *out receives the handle.
+ * Errors: LFLTS_ERR_ARG for out == NULL; LFLTS_ERR_CUDA if the device does not exist or cannot be
+ * selected; LFLTS_ERR_OOM if its small fixed device buffers cannot be allocated. */
 int lflts_create(lflts_ctx** out, int device);
 
-/* Free every device buffer and stream of the context, then the context. */
+/* Free every device buffer and stream of the context, then the context.
+ * Errors: none (a NULL context is accepted and ignored). */
 int lflts_destroy(lflts_ctx* ctx);
 
 /* Last error message of the context (never NULL; "" after success). */
@@ -126,6 +129,7 @@ int lflts_mesh_add(lflts_ctx* ctx, const double* xy, int64_t n_nodes,
  * [2] n_R (nodes the inner substeps update: P and its element neighbours),
  * [3] n_P, [4] n_tri, [5] K, [6] n_edges (edges with a nonzero stiffness
  * entry and a free endpoint), [7] n_edges_P (those with an endpoint in P).
+ * Errors: LFLTS_ERR_ARG for a NULL context or info, or an unknown mesh_id.
  */
 int lflts_mesh_info(lflts_ctx* ctx, int mesh_id, int64_t info[8]);
 
@@ -135,6 +139,7 @@ int lflts_mesh_info(lflts_ctx* ctx, int mesh_id, int64_t info[8]);
  * [P nodes | R \ P | other free nodes | Dirichlet nodes], each group in
  * Morton (Z-curve) order of the node coordinates, ties in the caller's order.
  * Works on host-only contexts (device -1).
+ * Errors: LFLTS_ERR_ARG for a NULL context or output, or an unknown mesh_id.
  */
 int lflts_mesh_order(lflts_ctx* ctx, int mesh_id, int32_t* new2old);
 
@@ -148,6 +153,7 @@ int lflts_mesh_order(lflts_ctx* ctx, int mesh_id, int32_t* new2old);
  *   out[4+2(m-1)] beta_m = T_{m-1}/T_{m+1},
  *   out[5+2(m-1)] c_m = 2 dt^2 beta_{m+1/2} / omega.
  * out must hold 4 + 2(p-1) doubles.
+ * Errors: LFLTS_ERR_ARG for out == NULL, p outside [1, 64], nu outside [0, 1] or dt <= 0.
  */
 int lflts_lts_constants(int p, double nu, double dt, double* out);
 
@@ -172,6 +178,8 @@ int lflts_interp_weights(const double* xy_c, int64_t n_c, const int32_t* tri_c, 
  * Register a nodal field (initial displacement u0 or velocity v0, Sec. 2.1)
  * on a mesh: values [n_nodes] FP64 in the caller's node order; values on
  * Dirichlet nodes are replaced by 0.
+ * Errors: LFLTS_ERR_ARG for NULL pointers, an unknown mesh_id or a non-finite value;
+ * LFLTS_ERR_OOM / LFLTS_ERR_CUDA from the upload.
  */
 int lflts_field_add(lflts_ctx* ctx, int mesh_id, const double* values, int* field_id);
 
@@ -180,6 +188,8 @@ int lflts_field_add(lflts_ctx* ctx, int mesh_id, const double* values, int* fiel
  * r(t) f(x), F_i = (f, phi_i); a point source at x_s has F_i = phi_i(x_s)) on
  * a mesh: nodes [n] node indices, weights [n] FP64.  It enters Alg. 2 through
  * w_n = A (I - P) z_n - F~(t_n), frozen over the inner substeps of a step.
+ * Errors: LFLTS_ERR_ARG for NULL pointers, n < 1, an unknown mesh_id, a node outside the mesh
+ * or a non-finite weight; LFLTS_ERR_OOM / LFLTS_ERR_CUDA from the upload.
  */
 int lflts_source_add(lflts_ctx* ctx, int mesh_id, const int32_t* nodes, const double* weights,
                      int64_t n, int* source_id);
@@ -187,6 +197,8 @@ int lflts_source_add(lflts_ctx* ctx, int mesh_id, const int32_t* nodes, const do
 /*
  * Register a linear QoI Q(u) = sum_k g[k] u[idx[k]] on a mesh (Sec. 2.1,
  * V = R).  idx [nnz] int32 node indices, g [nnz] FP64 weights.
+ * Errors: LFLTS_ERR_ARG for NULL pointers (with nnz > 0), nnz < 0, an unknown mesh_id, an
+ * index outside the mesh or a non-finite weight; LFLTS_ERR_OOM / LFLTS_ERR_CUDA from the upload.
  */
 int lflts_qoi_add(lflts_ctx* ctx, int mesh_id, const int32_t* idx,
                   const double* g, int64_t nnz, int* qoi_id);
@@ -226,6 +238,8 @@ int lflts_solve(lflts_ctx* ctx, const lflts_solve_desc* desc, const double* xi,
  * coarsest level), sums = {sum dQ, sum dQ^2, sum Qf, sum Qf^2} over the S
  * samples, FP64 with compensated (Neumaier) summation in a fixed order.
  * Qf, Qc [S] FP64; sums [4] FP64; all of the kind given by `mem`.
+ * Errors: LFLTS_ERR_ARG for a NULL context, Qf or sums, S < 1 or a bad mem kind;
+ * LFLTS_ERR_CUDA / LFLTS_ERR_OOM from the copies (host mode).
  */
 int lflts_level_sums(lflts_ctx* ctx, const double* Qf, const double* Qc,
                      int64_t S, double* sums, int mem, void* stream);
@@ -327,13 +341,16 @@ int lflts_profile_read(lflts_ctx* ctx, int kernel_class, int64_t* launches,
                        double* ms, double* alg_bytes);
 int lflts_launch_count(lflts_ctx* ctx, int64_t* launches);
 
-/* Set an LFLTS_OPT_* option of the context. */
+/* Set an LFLTS_OPT_* option of the context.
+ * Errors: LFLTS_ERR_ARG for a NULL context, an unknown option, a block budget below
+ * 1024 bytes or a fused-inner mode outside {0, 1, 2}. */
 int lflts_set_option(lflts_ctx* ctx, int option, int64_t value);
 
 /*
  * Counters: out[0] kernel launches executed (kernels inside replayed graphs
  * counted one by one), out[1] graph launches, out[2] kernel launches spent
  * in autotuning (not in out[0]), out[3] autotuned launch shapes cached.
+ * Errors: LFLTS_ERR_ARG for a NULL context or out.
  */
 int lflts_get_stats(lflts_ctx* ctx, int64_t out[4]);
 
