@@ -1712,6 +1712,7 @@ int lflts_level_sums(lflts_ctx* c, const double* Qf, const double* Qc, int64_t S
   c->err.clear();
   LF_TRY(set_device(c));
   if (!Qf || !sums || S < 1) return fail(c, LFLTS_ERR_ARG, "level_sums: null array or S < 1");
+  if (mem != LFLTS_MEM_HOST && mem != LFLTS_MEM_DEVICE) return fail(c, LFLTS_ERR_ARG, "level_sums: bad mem kind");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (mem == LFLTS_MEM_DEVICE) {
     Prof pr(c, st);
