@@ -1484,16 +1484,16 @@ int lflts_destroy(lflts_ctx* c) {
       for (auto& ge : w->graphs) cudaGraphExecDestroy(ge.exec);
     for (auto& w : c->ws)
       for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->W, &w->xipad, &w->xraw, &w->qps,
-                     &w->qpc, &w->Q, &w->uN})
+                     &w->qpc, &w->Q, &w->uN, &w->dts, &w->sig})
         if (b->p) cudaFree(b->p);
     for (Workspace* w : {c->gws.get()})
       if (w)
         for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->W, &w->xipad, &w->xraw, &w->qps,
-                       &w->qpc, &w->Q, &w->uN})
+                       &w->qpc, &w->Q, &w->uN, &w->dts, &w->sig})
           if (b->p) cudaFree(b->p);
     if (c->gb)
-      for (Buf* b : {&c->gb->ckpt, &c->gb->segU, &c->gb->rs, &c->gb->rho, &c->gb->gs, &c->gb->A, &c->gb->nua,
-                     &c->gb->nub, &c->gb->dnu, &c->gb->part, &c->gb->xraw, &c->gb->Q, &c->gb->G})
+      for (Buf* b : {&c->gb->ckpt, &c->gb->segU, &c->gb->rs, &c->gb->rho, &c->gb->gs, &c->gb->A, &c->gb->Aseg,
+                     &c->gb->nua, &c->gb->nub, &c->gb->dnu, &c->gb->part, &c->gb->xraw, &c->gb->Q, &c->gb->G})
         if (b->p) cudaFree(b->p);
     for (void* p : c->owned) cudaFree(p);
     for (auto s : c->streams) cudaStreamDestroy(s);
