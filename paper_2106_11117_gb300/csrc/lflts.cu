@@ -878,7 +878,9 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
   float best = 1e30f;
   const int64_t steps = std::min<int64_t>(4, ds.n_steps);
   for (int v : vecs) {
-    if (vecs.size() > 2 && v == 1) continue;
+    // one draw per thread is timed only for a small R (the fused kernel then
+    // gets four times as many CTAs for a small batch)
+    if (vecs.size() > 2 && v == 1 && !(n_R >= 1 && n_R <= 2048 && c->fused_mode >= 1 && !blocks)) continue;
     // The L2-blocked inner loop is not a candidate: on GB300 it measured
     // 10-35 % slower than one launch per substep at the benchmark shapes (the
     // launch count per step outweighs the DRAM bytes it saves).  The fused
