@@ -117,3 +117,51 @@ def field_bias_estimate(mean_L: np.ndarray, M_L: sp.csr_matrix, alpha: float) ->
     """Eq. bias_est in the V-norm (alpha the rate of ||E dQ_l||, as for the
     scalar QoI): ||mean dQ_L|| / (2^alpha - 1)."""
     return math.sqrt(l2_norm2(M_L, mean_L)) / (2.0**alpha - 1.0)
+
+
+def alg1_field(sample_level, eps, cost, N_init, mass, to_finest, alpha=2.0, L_max=None, L_start=2):
+    """Alg. 1 for a V-valued QoI (V = L2(D)), with the steps of the scalar
+    driver: the missing samples of every level, V_l by Eq. Vell_est in the
+    V-norm, N_l by Eq. optimal_Nl (never decreased), a new level while the
+    bias test of Eq. bias_est fails in the V-norm.
+
+    sample_level(l, offset, n) -> dU [n, n_nodes_l], nodal differences on
+        level l's mesh for draws offset..offset+n-1
+    cost(l) -> C_l;  N_init(l) -> initial N_l;  mass(l) -> M_l
+    to_finest(l, L) -> interpolation matrix from mesh l to mesh L (None if l == L)
+    Returns dict(estimate [n_nodes_L], L, N, V, bias, mse).
+    """
+    from . import mlmc as scalar
+
+    L = L_start
+    N = [int(N_init(l)) for l in range(L + 1)]
+    draws = [[] for _ in range(L + 1)]
+    done = [0] * (L + 1)
+    increased = True
+    while increased:
+        increased = False
+        for l in range(L + 1):
+            if N[l] > done[l]:
+                draws[l].extend(np.asarray(sample_level(l, done[l], N[l] - done[l]), dtype=np.float64))
+                done[l] = N[l]
+        stats = [field_mean_and_variance(*field_sums(np.array(draws[l]), mass(l)), done[l], mass(l))
+                 for l in range(L + 1)]
+        V = [v for _, v in stats]
+        C = [cost(l) for l in range(L + 1)]
+        Nopt = scalar.optimal_N([max(v, 0.0) for v in V], C, eps)
+        for l in range(L + 1):
+            if Nopt[l] > N[l]:
+                N[l] = Nopt[l]
+                increased = True
+        if field_bias_estimate(stats[L][0], mass(L), alpha) ** 2 >= eps**2 / 2.0 and (L_max is None or L < L_max):
+            L += 1
+            N.append(int(N_init(L)))
+            draws.append([])
+            done.append(0)
+            increased = True
+    stats = [field_mean_and_variance(*field_sums(np.array(draws[l]), mass(l)), done[l], mass(l))
+             for l in range(L + 1)]
+    V = [v for _, v in stats]
+    bias = field_bias_estimate(stats[L][0], mass(L), alpha)
+    est = mlmc_field_estimate([m for m, _ in stats], [to_finest(l, L) for l in range(L + 1)])
+    return {"estimate": est, "L": L, "N": done, "V": V, "bias": bias, "mse": scalar.mse_split(V, done, bias)}

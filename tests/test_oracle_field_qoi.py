@@ -104,3 +104,69 @@ def test_mlmc_field_estimate_telescopes_on_shared_draws():
     ML = mass_matrix(meshes[2].xy, meshes[2].tri)
     b = field_bias_estimate(means[2], ML, 2.0)
     assert b == pytest.approx(math.sqrt(l2_norm2(ML, means[2])) / 3.0, rel=1e-15)
+
+
+def test_alg1_field_reduces_to_the_scalar_driver():
+    """V = R (one node, M = [1]): the field driver takes the scalar driver's
+    decisions and returns its estimate."""
+    import scipy.sparse as sp
+
+    from oracle.field_qoi import alg1_field
+    from oracle.mlmc import alg1
+
+    rng = np.random.default_rng(7)
+    table = {l: rng.normal(2.0**(-2 * l), 2.0**(-1.5 * l), size=20000) for l in range(6)}
+
+    def sample(l, off, n):
+        return table[l][off:off + n]
+
+    kw = dict(eps=2e-3, cost=lambda l: 4.0**l, N_init=lambda l: 32, alpha=2.0, L_max=5)
+    a = alg1(sample, **kw)
+    b = alg1_field(lambda l, off, n: sample(l, off, n)[:, None], mass=lambda l: sp.identity(1, format="csr"),
+                   to_finest=lambda l, L: None, **kw)
+    assert b["L"] == a["L"] and b["N"] == a["N"]
+    assert b["estimate"][0] == pytest.approx(a["estimate"], rel=1e-13, abs=1e-15)
+    np.testing.assert_allclose(b["V"], a["V"], rtol=1e-10)
+
+
+def test_alg1_field_meets_its_tolerance_on_a_known_mean():
+    """Nested meshes, u_l = nodal values of f(x) + w1 g(x) + 4^-l w2 h(x) with
+    E w = 0: E[u_L] = f at the nodes of mesh L; the driver's estimate lies
+    within three of its own RMSE estimates of it in the L2 norm."""
+    from oracle.field_qoi import alg1_field
+
+    meshes = [square_mesh(4 * 2**l) for l in range(5)]
+    Ms = [mass_matrix(m.xy, m.tri) for m in meshes]
+    Ip = {}
+
+    def to_finest(l, L):
+        if l == L:
+            return None
+        if (l, L) not in Ip:
+            Ip[(l, L)] = interpolation_matrix(meshes[l].xy, meshes[l].tri, meshes[L].xy)
+        return Ip[(l, L)]
+
+    def u(m, l, w):
+        x, y = m.xy[:, 0], m.xy[:, 1]
+        return (np.sin(np.pi * x) * np.sin(np.pi * y) + w[0] * x * (1 - x)
+                + 4.0**(-l) * w[1] * np.cos(3 * x) * y)
+
+    W = np.random.default_rng(11).normal(size=(5, 4000, 2))
+
+    def sample(l, off, n):
+        m = meshes[l]
+        rows = []
+        for i in range(off, off + n):
+            d = u(m, l, W[l, i])
+            if l > 0:
+                d = d - to_finest(l - 1, l) @ u(meshes[l - 1], l - 1, W[l, i])
+            rows.append(d)
+        return np.array(rows)
+
+    r = alg1_field(sample, eps=0.05, cost=lambda l: 4.0**l, N_init=lambda l: 16,
+                   mass=lambda l: Ms[l], to_finest=to_finest, alpha=2.0, L_max=4)
+    L = r["L"]
+    x, y = meshes[L].xy[:, 0], meshes[L].xy[:, 1]
+    err = math.sqrt(l2_norm2(Ms[L], r["estimate"] - np.sin(np.pi * x) * np.sin(np.pi * y)))
+    assert r["mse"] <= 0.05**2 * 1.5
+    assert err <= 3 * math.sqrt(r["mse"])
