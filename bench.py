@@ -1,16 +1,22 @@
 """Benchmark: MLMC level-pair batch of stabilised LF-LTS solves on GB300.
 
-One step = one pass of the whole hot path over the batched workload
-square128-p8-K8-L5-fp32 (5 levels, 128^2 .. 2048^2 base cells, refined box
-8x (p = 8), K = 8 log-field terms, 8192/2048/512/128/32 samples per level as
-fine/coarse pairs on a shared draw): per-sample edge weights, Alg. 2 time
-loop to T = 1 on every mesh, QoI, dQ and FP64 level sums.  Solves on one
-mesh from the two pairs that use it run as one batch, meshes run on
-concurrent streams.
+Workload square128-p8-K8-L5-fp32: 5 levels, 128^2 .. 2048^2 base cells,
+refined box 8x (p = 8), K = 8 log-field terms, 8192/2048/512/128/32 samples
+per level as fine/coarse pairs on a shared draw; per-sample coefficients,
+Alg. 2 time loop to T = 1 on every mesh, QoI, dQ and FP64 level sums.
+Solves on one mesh from the two pairs that use it run as one batch, meshes
+run on concurrent streams.
 
-Metric: sample*DOF*substep/s = sum over solves of S * N_steps * (n_free + p*|R|)
+One bench step is one time slice of that whole batch (lflts_run_pairs_slice):
+step j advances every mesh's batch through the outer steps
+[floor(N k / n), floor(N (k+1) / n)), k = j mod n (n = --slices, default
+20), so n consecutive steps are exactly one complete MLMC batch; slice 0
+also forms the coefficients and start values, slice n-1 the QoI, dQ and
+level sums.  The timed K steps hold the units of their own slices.
+
+Metric: sample*DOF*substep/s = sum over solves of S * steps * (n_free + p*|R|)
 (each free DOF updated once per coarse step plus every DOF of the inner set
-R once per substep) divided by the step time.
+R once per substep) divided by the time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -189,18 +195,22 @@ def cpu_baseline(cfg_name, cores, n_rounds=1, pool=None):
 
 
 # ------------------------------------------------------------------- GPU
-def setup_gpu(cfg, rank):
-    import numpy as np
+def slice_steps(N, n_slices):
+    """Outer steps of each slice of an N-step time loop: slice k runs
+    [floor(N k / n), floor(N (k + 1) / n)) (the library's rule)."""
+    return [N * (k + 1) // n_slices - N * k // n_slices for k in range(n_slices)]
+
+
+def setup_gpu(cfg, rank, n_slices):
     import torch
     from paper_2106_11117_gb300 import build, lflts
     from workload import level_problem, xi_uniform
     build.build()
     ctx = lflts.Context(torch.cuda.current_device())
-    hs, levels = [], []
+    hs = []
     for l in range(cfg.levels):
         lev = level_problem(cfg, l)
         hs.append(ctx.add_level(lev))
-        levels.append(lev)
         del lev["mesh"]  # free host memory of large meshes
     prec = cfg.precision
     xis_h, xis_d, outs_d, outs_h = [], [], [], []
@@ -227,22 +237,48 @@ def setup_gpu(cfg, rank):
             j.S = S
             j.dQ, j.Qf, j.sums = o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr()
             js.append(j)
-        return js
+        return (lflts.PairJob * len(js))(*js)
 
-    units = 0
+    # solves per mesh: the fine solve of pair l and the coarse solve of pair
+    # l + 1 share mesh l and run as one batch
     solves = {}
     for l, S in enumerate(cfg.samples):
         solves[l] = solves.get(l, 0) + S
         if l > 0:
             solves[l - 1] = solves.get(l - 1, 0) + S
+    units_slice = [0] * n_slices
     for l, S in solves.items():
         info = hs[l].info
-        units += S * hs[l].n_steps * (info["n_free"] + cfg.p * info["n_R"])
-    h2d = sum(S * cfg.K * 8 for S in cfg.samples)
-    d2h = sum(S * 8 * 2 + 32 for S in cfg.samples)
-    return {"ctx": ctx, "hs": hs, "jobs_d": jobs(True), "jobs_h": jobs(False), "units": units,
-            "outs_d": outs_d, "outs_h": outs_h, "h2d": h2d, "d2h": d2h, "solves": solves,
+        per_step = S * (info["n_free"] + cfg.p * info["n_R"])
+        for k, n in enumerate(slice_steps(hs[l].n_steps, n_slices)):
+            units_slice[k] += per_step * n
+    h2d = sum(S * cfg.K * 8 for S in cfg.samples)             # xi, copied by slice 0
+    d2h = sum(S * 8 * 2 + 32 for S in cfg.samples)            # dQ, Qf, sums, by the last slice
+    return {"ctx": ctx, "hs": hs, "jobs_d": jobs(True), "jobs_h": jobs(False),
+            "units_slice": units_slice, "units_run": sum(units_slice), "outs_d": outs_d,
+            "outs_h": outs_h, "xis": (xis_h, xis_d), "h2d": h2d, "d2h": d2h, "solves": solves,
             "lflts": lflts}
+
+
+class SliceRunner:
+    """Bench steps: step j runs slice (j mod n) of the level-pair run, so n
+    consecutive steps are one complete MLMC batch of the workload (the
+    coefficients at slice 0, every outer step of every level once, the QoI,
+    dQ and level sums at slice n - 1)."""
+
+    def __init__(self, lf, ctx, jobs, n_slices, mem, stream, units_slice):
+        self.lf, self.ctx, self.jobs, self.n, self.mem, self.st = lf, ctx, jobs, n_slices, mem, stream
+        self.units_slice = units_slice
+        self.phase = 0
+        self.starts = self.ends = 0
+
+    def step(self):
+        k = self.phase
+        self.lf.lflts_run_pairs_slice(self.ctx.h, self.jobs, k, self.n, self.mem, self.st)
+        self.starts += k == 0
+        self.ends += k == self.n - 1
+        self.phase = (k + 1) % self.n
+        return self.units_slice[k]
 
 
 def run_ours(args):
@@ -258,23 +294,26 @@ def run_ours(args):
     pool = None  # the CPU baseline runs at N = 1 only (rank 0 of one process)
     if world == 1 and not args.no_cpu_baseline:
         pool = OraclePool(args.cpu_cores or os.cpu_count() or 1)
-    W = setup_gpu(cfg, rank)
+    n_sl = args.slices
+    W = setup_gpu(cfg, rank, n_sl)
     lf = W["lflts"]
     ctx = W["ctx"]
     st = torch.cuda.current_stream()
+    dev = SliceRunner(lf, ctx, W["jobs_d"], n_sl, lf.LFLTS_MEM_DEVICE, st.cuda_stream, W["units_slice"])
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    def step(device_mem=True):
-        if device_mem:
-            lf.lflts_run_pairs(ctx.h, W["jobs_d"], lf.LFLTS_MEM_DEVICE, st.cuda_stream)
-        else:
-            lf.lflts_run_pairs(ctx.h, W["jobs_h"], lf.LFLTS_MEM_HOST, st.cuda_stream)
+    def max_over_ranks(x):
+        if world > 1:
+            t = torch.tensor([x], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            x = float(t.item())
+        return x
 
     for _ in range(args.warmup):
-        step()
+        dev.step()
     torch.cuda.synchronize()
     barrier()
     clocks = Clocks(local)
@@ -283,60 +322,48 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    units = 0
     e0.record(st)
     for _ in range(args.steps):
-        step()
+        units += dev.step()
     e1.record(st)
     torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1))
     launches = lf.lflts_launch_count(ctx.h) - n0
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = W["units"] * world * args.steps / (ms * 1e-3)
+    value = units * world / (ms * 1e-3)
 
-    # end to end through the public API with host buffers (copies inside)
+    # end to end through the public API with host buffers: each step is the
+    # same slice call with pinned host xi and outputs (slice 0 copies xi in,
+    # the last slice copies dQ, Qf and the sums out; every call synchronises)
     e2e = None
     if not args.no_e2e:
+        host = SliceRunner(lf, ctx, W["jobs_h"], n_sl, lf.LFLTS_MEM_HOST, st.cuda_stream, W["units_slice"])
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
+        u_e2e = 0
         for _ in range(args.steps):
-            step(device_mem=False)
+            u_e2e += host.step()
         torch.cuda.synchronize()
         barrier()
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": W["units"] * world * args.steps / el, "unit": UNIT,
-               "h2d_bytes_per_step": W["h2d"] * world, "d2h_bytes_per_step": W["d2h"] * world}
+        el = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": u_e2e * world / el, "unit": UNIT,
+               "h2d_bytes_per_step": W["h2d"] * host.starts * world / args.steps,
+               "d2h_bytes_per_step": W["d2h"] * host.ends * world / args.steps,
+               "seconds": el, "runs_started": host.starts, "runs_completed": host.ends}
 
-    # one more step with per-launch CUDA events (each group's kernels timed on
-    # its own stream, groups queued whole) for the kernel split and roofline
+    # one more slice (slice 0 of a fresh run) with CUDA events around every
+    # launch, the batches one after another on one stream, for the kernel split
+    # and the roofline
     lf.lflts_profile_reset(ctx.h)
     lf.lflts_profile_enable(ctx.h, True)
-    step()
+    SliceRunner(lf, ctx, W["jobs_d"], n_sl, lf.LFLTS_MEM_DEVICE, st.cuda_stream, W["units_slice"]).step()
     torch.cuda.synchronize()
     lf.lflts_profile_enable(ctx.h, False)
     prof = {k: lf.lflts_profile_read(ctx.h, k) for k in ("init", "coarse", "inner", "qoi", "sums")}
-
-    # roofline of the dominant kernel class
-    peak, peak_kind = _peaks()
-    dom = max(("coarse", "inner"), key=lambda k: prof[k]["ms"])
-    pd = prof[dom]
-    achieved = pd["alg_bytes"] / (pd["ms"] * 1e-3) / 1e9 if pd["ms"] > 0 else 0.0
-    roof = {"bound": "hbm", "kernel": {"coarse": "k_coarse", "inner": "k_inner"}[dom],
-            "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": round(achieved / peak, 4),
-            "traffic": (TRAFFIC_RATIO[dom] * pd["alg_bytes"] / max(pd["launches"], 1)) if dom in TRAFFIC_RATIO else None,
-            "alg_bytes_per_launch": pd["alg_bytes"] / max(pd["launches"], 1),
-            "launches": pd["launches"], "avg_launch_ms": pd["ms"] / max(pd["launches"], 1),
-            "share_of_kernel_time": round(pd["ms"] / sum(v["ms"] for v in prof.values()), 4)}
+    roof = _roofline(prof, ("coarse", "inner"), {"coarse": "k_coarse", "inner": INNER_NAME})
 
     tte = None
     if world == 1 and not args.no_time_to_eps:
@@ -344,7 +371,7 @@ def run_ours(args):
 
     cpu = None
     if pool is not None:
-        cpu = cpu_baseline(args.config, pool.cores, pool=pool)
+        cpu = cpu_baseline(args.config, pool.cores, pool=pool, n_rounds=args.cpu_rounds)
         pool.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -352,18 +379,21 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if cfg.precision == 32 else "f64", "data": "synthetic",
                 "config": {"workload": _workload_desc(cfg),
+                           "step": f"one time slice of the whole level-pair batch: outer steps "
+                                   f"[floor(N k/{n_sl}), floor(N (k+1)/{n_sl})) of every mesh's batch, "
+                                   f"k = step mod {n_sl}; {n_sl} consecutive steps are one complete MLMC "
+                                   f"batch (coefficients at k = 0, QoI, dQ and FP64 level sums at "
+                                   f"k = {n_sl - 1})",
+                           "slices_per_batch": n_sl,
                            "solves_per_step": {f"mesh{l}": S for l, S in sorted(W["solves"].items())},
-                           "units_per_step": W["units"] * world,
+                           "units_timed": units * world, "units_per_batch": W["units_run"] * world,
                            "l2": "inputs larger than L2 (per-mesh state >= 1 GB), no flush",
                            "parallelism": f"samples sharded, dp{world}",
-                           "timing": "timed steps without per-launch events (solves replayed as CUDA "
-                                     "graphs on concurrent streams); roofline and kernel_classes from one "
-                                     "further step with CUDA events around every launch"},
+                           "timing": "timed steps without per-launch events (mesh batches on concurrent "
+                                     "streams); roofline and kernel_classes from one further slice with "
+                                     "CUDA events around every launch, batches one after another"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "time_to_eps": tte,
-                "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                                       "alg_GBps": round(v["alg_bytes"] / (v["ms"] * 1e-3) / 1e9, 1)
-                                       if v["ms"] > 0 else None} for k, v in prof.items()}}
+                "clocks": clk, "time_to_eps": tte, "kernel_classes": _classes_json(prof)}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -406,12 +436,8 @@ def time_to_eps(eps=2e-3):
         ctx.close()
 
 
-# DRAM traffic per launch = algorithmic bytes x (dram__bytes_read.sum +
-# dram__bytes_write.sum) / algorithmic bytes of one ncu capture of the same
-# kernel on a smaller batch (traffic grows in proportion to the draws): the
-# capture of k_inner on level 3 of the square128-p8-K8 hierarchy with 32 draws,
-# Morton node order, 644.1 MB of DRAM traffic for 619.0 MB algorithmic.
-TRAFFIC_RATIO = {"inner": 644.1 / 619.0}
+# Name of the inner kernel class in the roofline record.
+INNER_NAME = "k_inner (one launch per substep) / k_inner_fused"
 
 
 def _timed_passes(lf, ctx, step, st, warmup, steps, profile_steps=1, local=0):
@@ -446,7 +472,14 @@ def _timed_passes(lf, ctx, step, st, warmup, steps, profile_steps=1, local=0):
     return ms, launches, clk, prof
 
 
-def _roofline(prof, classes, names, traffic_ratio=None):
+def _roofline(prof, classes, names):
+    """Roofline record of the kernel class with the most device time:
+    achieved = algorithmic bytes / time over its launches (the library books
+    3 values per free node and coarse launch, 4 per node of R and inner
+    substep, 3 per node of R for a launch of all substeps; per-draw edge
+    weights not counted), against the measured HBM copy bandwidth.  traffic
+    (DRAM bytes per launch from ncu) is null here: the figures in profiles/
+    belong to captures of single launches, named there."""
     peak, peak_kind = _peaks()
     total = sum(v["ms"] for v in prof.values()) or 1.0
     dom = max(classes, key=lambda k: prof[k]["ms"])
@@ -454,9 +487,9 @@ def _roofline(prof, classes, names, traffic_ratio=None):
     achieved = pd["alg_bytes"] / (pd["ms"] * 1e-3) / 1e9 if pd["ms"] > 0 else 0.0
     per = pd["alg_bytes"] / max(pd["launches"], 1)
     return {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
-            "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": traffic_ratio * per if traffic_ratio else None, "alg_bytes_per_launch": per,
-            "launches": pd["launches"], "avg_launch_ms": pd["ms"] / max(pd["launches"], 1),
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "alg_bytes_per_launch": per, "launches": pd["launches"],
+            "avg_launch_ms": pd["ms"] / max(pd["launches"], 1),
             "share_of_kernel_time": round(pd["ms"] / total, 4)}
 
 
@@ -752,14 +785,18 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--slices", type=int, default=20,
+                    help="time slices per level-pair batch (one bench step = one slice)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["batched", "plain", "bandwidth", "lshape", "adjoint"],
                     default="batched")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cores", type=int, default=0)
+    ap.add_argument("--cpu-rounds", type=int, default=8,
+                    help="level-0 oracle solves per host core in the CPU baseline")
     ap.add_argument("--no-time-to-eps", action="store_true")
     ap.add_argument("--eps", type=float, default=2e-3)
     ap.add_argument("--profile-case", type=int, default=-1,

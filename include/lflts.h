@@ -77,11 +77,6 @@ enum {
   LFLTS_OPT_AUTOTUNE = 2, /* 1 (default): the first solve of a (mesh, S, precision, p) times the
                              candidate launch shapes (draws per thread, CTAs per SM, register cap)
                              and keeps the best */
-  LFLTS_OPT_BLOCKED = 3,  /* 1: run the inner substeps in L2 blocks (block cores with halos of P
-                             nodes, draw slabs, all substeps of a block back to back; same results
-                             bit for bit, fewer DRAM bytes, more launches); 0 (default): one launch
-                             per substep over R */
-  LFLTS_OPT_BLOCK_BUDGET = 4, /* bytes of inner-loop working set per L2 block (default 40e6) */
   LFLTS_OPT_FUSED_INNER = 5   /* all p-1 inner substeps of a step in one launch, with R's recursion,
                                  coupling slots, their edge weights and 1/m for a CTA's draws in
                                  shared memory (only where they fit in 200 KB; same results bit for
@@ -276,6 +271,32 @@ int lflts_run_pairs(lflts_ctx* ctx, const lflts_pair_job* jobs, int n_jobs,
                     int mem, void* stream);
 
 /*
+ * lflts_run_pairs in time slices (the same computation, cut along the time
+ * axis of Alg. 2): the time loop of every merged batch, N outer steps (the
+ * longest segment's count in a ragged batch), is split into n_slices parts,
+ * and call `slice` (0 <= slice < n_slices) queues the outer steps
+ * [floor(N slice / n_slices), floor(N (slice + 1) / n_slices)) of every batch.
+ * Call 0 also copies the draws and forms the coefficients and start values;
+ * call n_slices - 1 also forms the QoI, dQ, Qf and the level sums.  Calls
+ * 0, 1, ..., n_slices - 1 in order, with the same jobs (same descriptors,
+ * pointers and S), the same memory kind and the same n_slices, give exactly
+ * the results of one lflts_run_pairs call (bit for bit); between them the
+ * state stays on the device in the context.  lflts_run_pairs is
+ * lflts_run_pairs_slice(..., 0, 1, ...).  Sliced runs are never captured
+ * into CUDA graphs.  Host memory (mem = LFLTS_MEM_HOST): call 0 reads xi,
+ * the last call writes dQ, Qf and sums; every call synchronises `stream`
+ * before it returns.  A call with slice = 0 starts a new run and drops an
+ * unfinished one; so does lflts_run_pairs.  The jobs' buffers must stay
+ * valid until the last call has completed.
+ * Errors: those of lflts_run_pairs; LFLTS_ERR_ARG for slice outside
+ * [0, n_slices) or a call that does not continue the run in progress (other
+ * jobs, memory kind or n_slices, or slices out of order).  After an error the
+ * run is dropped.
+ */
+int lflts_run_pairs_slice(lflts_ctx* ctx, const lflts_pair_job* jobs, int n_jobs,
+                          int mem, int slice, int n_slices, void* stream);
+
+/*
  * Gradient of the QoI with respect to the field parameters: for every draw
  * s, Q[s] (as lflts_solve) and dQdxi[s][k] = dQ/dxi_k, the exact derivative of
  * the computed (discrete) QoI.  Discrete adjoint of the u-form LF-LTS solve:
@@ -298,13 +319,18 @@ int lflts_grad_xi(lflts_ctx* ctx, const lflts_solve_desc* desc, const double* xi
 /*
  * QoI reduction that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot let a library allocate device
- * memory (their memory is owned by their own pool allocator, they must not
- * allocate after start-up, or they are recording work into a CUDA graph,
- * where cudaMalloc is not permitted).  It computes, like the QoI step of
- * lflts_solve,
+ * memory: applications whose device memory is owned by their own pool
+ * allocator (a library cudaMalloc would fragment it or exceed its budget),
+ * or code that must not allocate once it is running (fixed memory plans,
+ * latency-bound loops in which a cudaMalloc would synchronise the device).
+ * It computes, like the QoI step of lflts_solve,
  *     Q[s] = sum_k g[k] * u[idx[k]][s],   s = 0 .. S-1,
- * in FP64 with compensated summation in the same order as lflts_solve.
- *   ctx        optional (may be NULL); receives the error message
+ * in FP64 with compensated summation in the same order as lflts_solve
+ * (for the same u and weights the two give the same Q bit for bit).
+ *   ctx        optional (may be NULL); receives the error message.  With a
+ *              context of a device, that device is made current for the
+ *              call; with NULL (or a host-only context) the current device
+ *              is used
  *   u          device [n_rows][S] state, FP32 (precision 32) or FP64 (64)
  *   idx, g     device [nnz] row indices and FP64 weights; an index outside
  *              [0, n_rows) is skipped (contributes nothing) and never read
@@ -319,7 +345,13 @@ int lflts_grad_xi(lflts_ctx* ctx, const lflts_solve_desc* desc, const double* xi
  * calls on a device share the array and every call overwrites what it
  * reads, so nothing needs clearing, but calls whose kernels overlap on the
  * GPU (different streams, no ordering between them) race on it.  The call
- * makes no cudaMalloc/cudaFree and no allocating library call.
+ * makes no cudaMalloc/cudaFree and no allocating library call.  Unlike
+ * lflts_solve it does not check Q: a non-finite Q[s] is written as it is and
+ * the call still returns LFLTS_OK.
+ * Errors: LFLTS_ERR_ARG for null pointers, sizes below 1, a precision other
+ * than 32/64 or a call beyond the scratch limit; LFLTS_ERR_CUDA if the
+ * device cannot be selected, the array's address cannot be resolved or a
+ * launch fails.
  */
 int lflts_qoi_reduce_noalloc(lflts_ctx* ctx, const void* u, int precision, int64_t n_rows,
                              int64_t S, const int32_t* idx, const double* g, int64_t nnz,
@@ -329,9 +361,13 @@ int lflts_qoi_reduce_noalloc(lflts_ctx* ctx, const void* u, int precision, int64
  * Profiling.  When enabled, every kernel launch is bracketed by CUDA events
  * on its stream; lflts_profile_read synchronises the context's device and
  * returns, per kernel class, the launch count, the summed device time in ms
- * and the summed algorithmic bytes (the state traffic the method must move:
- * per node and sample, FP32 state counts 4 bytes per value read or written;
- * see the kernel class comments in the implementation).  Reset clears the
+ * and the summed algorithmic bytes: the state values the method must move per
+ * node and draw (4 bytes each in FP32, 8 in FP64), counted as 3 values per
+ * free node for a coarse launch (u_n and u_{n-1} read, u_{n+1} written), 4
+ * per node of R for one inner substep (r_m, r_{m-1} and g read, r_{m+1}
+ * written) and 3 per node of R for a launch that runs all substeps of a step
+ * on chip; per-draw edge weights and index data are not counted (the
+ * coefficient can be recomputed from xi).  Reset clears the
  * counters.  lflts_launch_count returns all kernel launches of the context
  * since creation, whether profiling is on or not.
  */
@@ -342,8 +378,8 @@ int lflts_profile_read(lflts_ctx* ctx, int kernel_class, int64_t* launches,
 int lflts_launch_count(lflts_ctx* ctx, int64_t* launches);
 
 /* Set an LFLTS_OPT_* option of the context.
- * Errors: LFLTS_ERR_ARG for a NULL context, an unknown option, a block budget below
- * 1024 bytes or a fused-inner mode outside {0, 1, 2}. */
+ * Errors: LFLTS_ERR_ARG for a NULL context, an unknown option or a fused-inner mode
+ * outside {0, 1, 2}. */
 int lflts_set_option(lflts_ctx* ctx, int option, int64_t value);
 
 /*

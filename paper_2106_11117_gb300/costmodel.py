@@ -54,49 +54,3 @@ def solve_work(n_steps, n_free, n_R, p, scheme):
     if scheme == "lts":
         return n_steps * (n_free + p * n_R)
     return p * n_steps * n_free
-
-
-# ---------------------------------------------------------------------------
-# Graded meshes T_{m,s} (Sec. 3.5): m layers, grading s, the first q layers
-# form the region of the small step.
-# ---------------------------------------------------------------------------
-def cost_lf_graded(m, d, s):
-    """Eq. cost_waveeq_LFgraded: elements / h_1 ~ m^{s+d}."""
-    return float(m) ** (s + d)
-
-
-def cost_lts_graded(m, d, s, q):
-    """Eq. cost_waveeq_LTSgraded: the first q layers step with h_1, the rest
-    with h_{q+1} ~ ((q+1)^s - q^s) / m^s."""
-    g = (q + 1.0) ** s - float(q) ** s
-    return (float(m) ** (s + d) + float(m) ** s * float(q) ** d * (g - 1.0)) / g
-
-
-def speedup_graded(m, d, s, q):
-    """Eq. speedup_det_graded: one LF solve over one LTS solve."""
-    g = (q + 1.0) ** s - float(q) ** s
-    return float(m) ** d * g / (float(m) ** d + float(q) ** d * (g - 1.0))
-
-
-def ddq_speedup_graded(m, d, s, q):
-    """Left-hand side of Eq. ddqS: the numerator of d/dq of speedup_graded
-    (its sign is the sign of the derivative)."""
-    g = (q + 1.0) ** s - q**s
-    gp = (q + 1.0) ** (s - 1) - q ** (s - 1)
-    md = float(m) ** d
-    return (s * gp * (md + q**d * (g - 1.0))
-            - g * q ** (d - 1) * (d * (g - 1.0) + s * q * gp))
-
-
-def q_opt_graded(m, d, s):
-    """Integer number of fine layers q in [1, m] with the largest speed-up."""
-    return max(range(1, int(m) + 1), key=lambda q: speedup_graded(m, d, s, q))
-
-
-def graded_rates(d, s, k=1):
-    """Cost exponents of Cor. cor:totalcostLFgraded and the rate of the
-    speed-up in Eq. Qeff_graded for beta < s + d^2/(d+s-1):
-    (gamma_LF, gamma_LTS, exponent e of S = O(eps^-e)), k the order."""
-    g_lf = s + d
-    g_lts = s + d * d / (d + s - 1.0)
-    return g_lf, g_lts, d * (s - 1.0) / ((k + 1.0) * (s + d - 1.0))

@@ -287,26 +287,20 @@ k_coarse(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W, const Real*
 // r_m = s_cur * cur, r_{m-1} = s_prev * prev (prev == nullptr: r_0 = 0).
 // LAST: fold r_p into d and u_next instead of storing it.
 // ---------------------------------------------------------------------------
-// LIST: the launch covers the nodes list[0..n_items) (an L2 block of the
-// inner loop) and the draws [s_lo, s_lo + s_cnt); otherwise all of R and all
-// draws.  The arithmetic per node and draw is the same either way.
-template <typename Real, int VEC, bool LAST, int MINB = 1, bool LIST = false, bool RAG = false>
+template <typename Real, int VEC, bool LAST, int MINB = 1, bool RAG = false>
 __global__ void __launch_bounds__(256, MINB)
 k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
         const Real* __restrict__ cur, Real s_cur, const Real* __restrict__ prev, Real s_prev,
         Real* __restrict__ r_next, const Real* __restrict__ g, const Real* __restrict__ u,
         Real* __restrict__ u_next, Real* __restrict__ d, Real one_plus_beta, Real beta, Real cm,
-        Real kappa, int S_lim, const int* __restrict__ list = nullptr, int n_items = 0, int s_lo = 0,
-        int s_cnt = 0) {
+        Real kappa, int S_lim) {
   const Lane l = lane_of(SB);
-  const int s0 = (LIST ? s_lo : 0) + l.sv * VEC;
+  const int s0 = l.sv * VEC;
   const int lim = RAG ? S_lim : S;
-  if (s0 >= (LIST ? s_lo + s_cnt : lim)) return;
+  if (s0 >= lim) return;
   const int nvalid = lim - s0;
   const int nP = m.n_P;
-  const int n_loop = LIST ? n_items : m.n_R;
-  for (int t = blockIdx.x * l.NB + l.row; t < n_loop; t += gridDim.x * l.NB) {
-    const int i = LIST ? __ldg(list + t) : t;
+  for (int i = blockIdx.x * l.NB + l.row; i < m.n_R; i += gridDim.x * l.NB) {
     const size_t is = (size_t)i * S + s0;
     const bool iP = i < nP;
     // issue every independent load of this node before any arithmetic
@@ -582,7 +576,9 @@ __global__ void k_qoi_partial(const Real* __restrict__ u, int S, const int* __re
   const int c = blockIdx.x;
   const int k0 = c * chunk, k1 = min(nnz, k0 + chunk);
   Neumaier acc;
-  for (int k = k0; k < k1; ++k) acc.add(gw[k] * (double)u[(size_t)idx[k] * S + s]);
+  // the product is rounded on its own (no fused multiply-add), so that every
+  // reduction of the same values gives the same Q bit for bit
+  for (int k = k0; k < k1; ++k) acc.add(__dmul_rn(gw[k], (double)u[(size_t)idx[k] * S + s]));
   ps[(size_t)c * S + s] = acc.s;
   pc[(size_t)c * S + s] = acc.c;
 }

@@ -59,12 +59,6 @@ struct MeshGPU {
   int64_t n_rslots = -1;
   // autotuned (vec, shape code) per (S, precision, p)
   std::map<std::tuple<int64_t, int, int>, std::pair<int, int>> tuned;
-  // L2 blocks of the inner loop per (S, precision, p), uploaded lists
-  struct DevBlocks {
-    InnerBlocks h;
-    int* d_nodes = nullptr;
-  };
-  std::map<std::tuple<int64_t, int, int>, DevBlocks> blocks;
 };
 
 struct Field {
@@ -129,6 +123,8 @@ struct ProfRec {
   double bytes;
 };
 
+struct PairRun;  // a level-pair batch between the calls of a sliced run
+
 }  // namespace
 
 struct lflts_ctx {
@@ -157,10 +153,10 @@ struct lflts_ctx {
   int64_t graph_launches = 0;
   bool graphs = true;
   bool autotune = true;
-  bool force_blocked = false;
-  double block_budget = 40.0e6;  // bytes of inner-loop working set per L2 block
   int fused_mode = 1;            // fused inner kernel: 0 never, 1 autotuned, 2 always where it fits
   std::vector<void*> owned;  // device allocations of meshes, fields, QoIs
+  std::unique_ptr<PairRun> run;  // lflts_run_pairs_slice: the run in progress, if any
+  ~lflts_ctx();
 };
 
 namespace {
@@ -396,13 +392,11 @@ struct Stepper {
   double delta = 0, omega = 0, c0 = 0, gamma = 0;
   int p = 1, n_R = 0;
   int64_t S = 0;
-  double Srb = 0, coarse_bytes = 0, edgeP_bytes = 0;
+  double Srb = 0, coarse_bytes = 0;
   const Real* W = nullptr;
   Real* g = nullptr;
   Real* rbuf[3] = {nullptr, nullptr, nullptr};
   bool minb6 = false;
-  const InnerBlocks* blk = nullptr;  // L2 blocks (null: one launch per substep over R)
-  const int* blk_nodes = nullptr;
   int cps = 16;
   bool fused = false;  // all inner substeps in one launch (R in shared memory)
   int fSB = 1;
@@ -446,8 +440,7 @@ struct Stepper {
     gc = geometry_vec(c, h.n_free, S, VEC, cta_per_sm);
     gi = geometry_vec(c, std::max(n_R, 1), S, VEC, cta_per_sm);
     Srb = double(S) * sizeof(Real);
-    coarse_bytes = Srb * (4.0 * h.n_free - 2.0 * n_R + double(h.n_edges));
-    edgeP_bytes = Srb * double(h.n_edges_P);
+    coarse_bytes = 3.0 * Srb * double(h.n_free);
     if (shape >= 2000 && n_R > 0 && p > 1 && p <= 64) {
       fused_plan(c, n_R, mg.n_rslots, S, VEC, sizeof(Real), fSB, fsmem);
       fused = fsmem > 0;
@@ -471,8 +464,7 @@ struct Stepper {
     gc = geometry_vec(c, h.n_free, S_act, VEC, cps);
     gi = geometry_vec(c, std::max(n_R, 1), S_act, VEC, cps);
     Srb = double(S_act) * sizeof(Real);
-    coarse_bytes = Srb * (4.0 * h.n_free - 2.0 * n_R + double(h.n_edges));
-    edgeP_bytes = Srb * double(h.n_edges_P);
+    coarse_bytes = 3.0 * Srb * double(h.n_free);
     if (fused) {
       const int64_t SL = int64_t(fSB) * VEC;
       fgrid = static_cast<int>((S_act + SL - 1) / SL);
@@ -490,59 +482,6 @@ struct Stepper {
       rf.n = static_cast<int>(n);
     }
     return rf;
-  }
-
-  // The p-1 substeps block by block: all substeps of one (node block, draw
-  // slab) run back to back so that their r, g and W stay in L2.  Substep m
-  // covers the block's core and its first p-1-m halo layers; the last one
-  // updates d and u on the core only.  Algorithmic bytes are booked for the
-  // core (the halo is recomputation).
-  int inner_blocked(const Real* uc, Real* un, Real* d, Real kappa, cudaStream_t st) {
-    const int64_t nb = static_cast<int64_t>(blk->start.size()) - 1;
-    const int64_t slab = blk->slab;
-    for (int64_t s_lo = 0; s_lo < S; s_lo += slab) {
-      const int s_cnt = static_cast<int>(std::min<int64_t>(slab, S - s_lo));
-      for (int64_t b = 0; b < nb; ++b) {
-        const int* list = blk_nodes + blk->start[b];
-        const int32_t core = blk->layer_end[b * (p - 1)];
-        const Real* cur = g;
-        Real s_cur = (Real)(-c0);
-        const Real* prev = nullptr;
-        Real s_prev = Real(0);
-        int nxt = 0;
-        for (int m = 1; m < p; ++m) {
-          const bool last = (m == p - 1);
-          const int32_t len = blk->layer_end[b * (p - 1) + (p - 1 - m)];
-          const Geo gb = geometry(c, len, s_cnt / VEC, cps);
-          const Real opb = (Real)(1.0 + beta[m]), bt = (Real)beta[m], cmm = (Real)cm[m];
-          Real* rn = rbuf[nxt];
-          Prof pr(c, st);
-#define LF_INNER_B(L, B)                                                                                    \
-  k_inner<Real, VEC, L, B, true><<<gb.grid, 256, 0, st>>>(md, (int)S, gb.SB, W, cur, s_cur, prev, s_prev, rn, \
-                                                          g, uc, un, d, opb, bt, cmm, kappa, (int)S, list,     \
-                                                          len, (int)s_lo, s_cnt)
-          if (last) {
-            if (minb6) LF_INNER_B(true, 6);
-            else LF_INNER_B(true, 1);
-          } else {
-            if (minb6) LF_INNER_B(false, 6);
-            else LF_INNER_B(false, 1);
-          }
-#undef LF_INNER_B
-          LF_CUDA(c, cudaGetLastError());
-          const double reads = (m == 1 ? 1.0 : (m == 2 ? 2.0 : 3.0));
-          const double per_node = reads + (last ? 4.0 : 1.0);
-          const double share = double(core) / double(n_R) * double(s_cnt) / double(S);
-          pr.end(LFLTS_KERNEL_INNER, (per_node * n_R * Srb + edgeP_bytes) * share);
-          prev = cur;
-          s_prev = s_cur;
-          cur = rn;
-          s_cur = Real(1);
-          nxt = (nxt + 1) % 3;
-        }
-      }
-    }
-    return 0;
   }
 
   // u_next = 2 T u_cur - u_prev in increments: d += kappa r_p, u_next = u_cur + d.
@@ -571,7 +510,6 @@ struct Stepper {
       LF_CUDA(c, cudaGetLastError());
       pr.end(LFLTS_KERNEL_COARSE, coarse_bytes);
     }
-    if (n_R > 0 && blk) return inner_blocked(uc, un, d, kappa, st);
     if (n_R > 0 && fused) {
       Prof pr(c, st);
       const int ns = static_cast<int>(mgp->n_rslots);
@@ -582,8 +520,8 @@ struct Stepper {
         k_inner_fused<Real, VEC, false><<<fgrid, 256, fsmem, st>>>(md, (int)S, fSB, W, g, uc, un, d, coef, kappa,
                                                                    (int)S_act, mgp->rptr, mgp->rslot, ns);
       LF_CUDA(c, cudaGetLastError());
-      // g, u and d in, d and u out on R, the P-edge weights: once per step
-      pr.end(LFLTS_KERNEL_INNER, 5.0 * n_R * Srb + edgeP_bytes);
+      // all substeps on chip: the outer-step bytes of R remain
+      pr.end(LFLTS_KERNEL_INNER, 3.0 * n_R * Srb);
       return 0;
     }
     if (n_R > 0) {
@@ -599,7 +537,7 @@ struct Stepper {
         Real* rn = rbuf[nxt];
         Prof pr(c, st);
 #define LF_INNER(L, B, RG)                                                                                     \
-  k_inner<Real, VEC, L, B, false, RG><<<gi.grid, 256, 0, st>>>(md, (int)S, gi.SB, W, cur, s_cur, prev, s_prev, rn, \
+  k_inner<Real, VEC, L, B, RG><<<gi.grid, 256, 0, st>>>(md, (int)S, gi.SB, W, cur, s_cur, prev, s_prev, rn, \
                                                                g, uc, un, d, opb, bt, cmm, kappa, (int)S_act)
         if (dts) {  // ragged batch: only the last substep writes u and d
           if (last) LF_INNER(true, 1, true);
@@ -613,10 +551,8 @@ struct Stepper {
         }
 #undef LF_INNER
         LF_CUDA(c, cudaGetLastError());
-        // values per R node: cur, prev (unless it is g), g, the new r (or d, u in, d, u out)
-        const double reads = (m == 1 ? 1.0 : (m == 2 ? 2.0 : 3.0));
-        const double per_node = reads + (last ? 4.0 : 1.0);
-        pr.end(LFLTS_KERNEL_INNER, per_node * n_R * Srb + edgeP_bytes);
+        // per R node r_m, r_{m-1} and g read, r_{m+1} written
+        pr.end(LFLTS_KERNEL_INNER, 4.0 * n_R * Srb);
         prev = cur;
         s_prev = s_cur;
         cur = rn;
@@ -633,15 +569,11 @@ struct Stepper {
 template <typename Real, int VEC>
 int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S,
               Workspace& ws, Real*& uc_out, cudaStream_t st, int cta_per_sm = 16, int64_t n_steps = -1,
-              const MeshGPU::DevBlocks* blocks = nullptr, const double* dts = nullptr) {
+              const double* dts = nullptr) {
   Stepper<Real, VEC> stp(c, ds, mg, n_R, S, static_cast<const Real*>(ws.W.p), static_cast<Real*>(ws.g.p),
                          static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p),
                          cta_per_sm);
   stp.dts = dts;  // a ragged batch: its kernels (all draws active)
-  if (blocks && cta_per_sm >= 1000 && cta_per_sm < 2000) {
-    stp.blk = &blocks->h;
-    stp.blk_nodes = blocks->d_nodes;
-  }
   Real* uc = static_cast<Real*>(ws.ua.p);
   Real* un = static_cast<Real*>(ws.ub.p);
   Real* d = static_cast<Real*>(ws.d.p);
@@ -654,50 +586,13 @@ int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n
   return 0;
 }
 
-// L2 blocks of the inner loop for a batch (built and uploaded once per
-// (S, precision, p)): a block's working set (three r, g and the weights of
-// about two P edges per node and draw) is kept under about 40 MB.
-template <typename Real>
-int get_blocks(lflts_ctx* c, MeshGPU& mg, int64_t S, int p, const MeshGPU::DevBlocks*& out) {
-  out = nullptr;
-  const HostMesh& h = mg.h;
-  if (p < 2 || h.n_R == 0) return 0;
-  const auto key = std::make_tuple(S, int(sizeof(Real) * 8), p);
-  auto it = mg.blocks.find(key);
-  if (it != mg.blocks.end()) {
-    out = &it->second;
-    return 0;
-  }
-  const double budget = c->block_budget, f = 6.0 * sizeof(Real);
-  MeshGPU::DevBlocks db;
-  int64_t core = h.n_R;
-  // slabs of at least 32 draws (a full 128-byte row per node and array);
-  // below that the node blocks shrink instead
-  if (double(h.n_R) * S * f <= budget) {
-    db.h.slab = S;
-  } else {
-    const int64_t slab_max = static_cast<int64_t>(budget / (double(h.n_R) * f)) / 8 * 8;
-    if (slab_max >= std::min<int64_t>(32, S)) {
-      db.h.slab = std::min<int64_t>(slab_max, S);
-    } else {
-      db.h.slab = std::min<int64_t>(32, S);
-      core = std::max<int64_t>(1, static_cast<int64_t>(budget / (double(db.h.slab) * f * 1.15)));
-    }
-  }
-  build_inner_blocks(h, p, core, db.h);
-  LF_TRY(upload(c, &db.d_nodes, db.h.nodes.data(), db.h.nodes.size()));
-  auto res = mg.blocks.emplace(key, std::move(db));
-  out = &res.first->second;
-  return 0;
-}
-
 template <typename Real>
 int time_loop_vec(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
                   Real*& uc, cudaStream_t st, int vec, int cps, int64_t n_steps = -1,
-                  const MeshGPU::DevBlocks* blocks = nullptr, const double* dts = nullptr) {
-  if (vec == 4) return time_loop<Real, 4>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks, dts);
-  if (vec == 2) return time_loop<Real, 2>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks, dts);
-  return time_loop<Real, 1>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, blocks, dts);
+                  const double* dts = nullptr) {
+  if (vec == 4) return time_loop<Real, 4>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, dts);
+  if (vec == 2) return time_loop<Real, 2>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, dts);
+  return time_loop<Real, 1>(c, ds, mg, n_R, S, ws, uc, st, cps, n_steps, dts);
 }
 
 // Whether the fused inner kernel can run this batch; raises its dynamic
@@ -759,6 +654,7 @@ struct SliceTask {
   virtual ~SliceTask() = default;
   virtual int advance(int64_t steps) = 0;  // queue up to `steps` more outer steps
   virtual bool done() const = 0;
+  virtual int64_t position() const = 0;    // outer steps queued so far
   virtual int finish() = 0;                // queue the QoI of the last segments
 };
 
@@ -781,7 +677,7 @@ struct SlicedLoop : SliceTask {
   size_t active;  // segments 0 .. active-1 still step
   LoopOut<Real> out;
   SlicedLoop(lflts_ctx* c_, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
-             cudaStream_t st_, int cps, const MeshGPU::DevBlocks* blocks, const RaggedSpec* rg, LoopOut<Real> o)
+             cudaStream_t st_, int cps, const RaggedSpec* rg, LoopOut<Real> o)
       : c(c_),
         stp(c_, ds, mg, n_R, S, static_cast<const Real*>(ws.W.p), static_cast<Real*>(ws.g.p),
             static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p), cps),
@@ -791,10 +687,6 @@ struct SlicedLoop : SliceTask {
         N(ds.n_steps),
         st(st_),
         out(std::move(o)) {
-    if (blocks && cps >= 1000 && cps < 2000) {
-      stp.blk = &blocks->h;
-      stp.blk_nodes = blocks->d_nodes;
-    }
     if (rg) {
       segs = rg->segs;
       stp.dts = rg->d_dts;
@@ -824,6 +716,7 @@ struct SlicedLoop : SliceTask {
     return 0;
   }
   bool done() const override { return n >= N; }
+  int64_t position() const override { return n; }
   int finish() override {
     LF_TRY(freeze());
     return out.qoi_final();
@@ -833,31 +726,30 @@ struct SlicedLoop : SliceTask {
 template <typename Real>
 std::unique_ptr<SliceTask> make_sliced(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R,
                                        int64_t S, Workspace& ws, cudaStream_t st, int vec, int cps,
-                                       const MeshGPU::DevBlocks* blocks, const RaggedSpec* rg, LoopOut<Real> o) {
+                                       const RaggedSpec* rg, LoopOut<Real> o) {
   if (vec == 4)
-    return std::make_unique<SlicedLoop<Real, 4>>(c, ds, mg, n_R, S, ws, st, cps, blocks, rg, std::move(o));
+    return std::make_unique<SlicedLoop<Real, 4>>(c, ds, mg, n_R, S, ws, st, cps, rg, std::move(o));
   if (vec == 2)
-    return std::make_unique<SlicedLoop<Real, 2>>(c, ds, mg, n_R, S, ws, st, cps, blocks, rg, std::move(o));
-  return std::make_unique<SlicedLoop<Real, 1>>(c, ds, mg, n_R, S, ws, st, cps, blocks, rg, std::move(o));
+    return std::make_unique<SlicedLoop<Real, 2>>(c, ds, mg, n_R, S, ws, st, cps, rg, std::move(o));
+  return std::make_unique<SlicedLoop<Real, 1>>(c, ds, mg, n_R, S, ws, st, cps, rg, std::move(o));
 }
 
 // Launch shape of the step kernels for a batch: draws per thread (vec),
 // CTAs per SM and the register cap.  Shape code cps: CTAs per SM, +100 for
-// the instantiation limited to 40 registers (6 CTAs of 256 per SM), +1000
-// for the L2-blocked inner loop (opt-in only), +2000 for the fused inner
-// kernel.  With autotuning on, the first solve of a (mesh, S, precision, p)
+// the instantiation limited to 40 registers (6 CTAs of 256 per SM), +2000
+// for the fused inner kernel.  With autotuning on, the first solve of a (mesh, S, precision, p)
 // times every candidate over a few steps on the real buffers (the state is
 // re-initialised afterwards) and keeps the fastest.
 template <typename Real>
 int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
-                 cudaStream_t st, int& vec, int& cps, const MeshGPU::DevBlocks* blocks, const double* dts) {
+                 cudaStream_t st, int& vec, int& cps, const double* dts) {
   const int vmax = (sizeof(Real) == 4) ? 4 : 2;
   std::vector<int> vecs;
   for (int v = vmax; v >= 1; v /= 2)
     if (S % v == 0) vecs.push_back(v);
   vec = vecs.front();
   cps = 16;
-  if (c->fused_mode == 2 && !blocks && fused_ok<Real>(c, mg, n_R, S, vec, ds.p)) {
+  if (c->fused_mode == 2 && fused_ok<Real>(c, mg, n_R, S, vec, ds.p)) {
     cps = 2016;
     return 0;
   }
@@ -880,24 +772,21 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
   for (int v : vecs) {
     // one draw per thread is timed only for a small R (the fused kernel then
     // gets four times as many CTAs for a small batch)
-    if (vecs.size() > 2 && v == 1 && !(n_R >= 1 && n_R <= 2048 && c->fused_mode >= 1 && !blocks)) continue;
-    // The L2-blocked inner loop is not a candidate: on GB300 it measured
-    // 10-35 % slower than one launch per substep at the benchmark shapes (the
-    // launch count per step outweighs the DRAM bytes it saves).  The fused
-    // inner kernel is, where R fits in shared memory.
+    if (vecs.size() > 2 && v == 1 && !(n_R >= 1 && n_R <= 2048 && c->fused_mode >= 1)) continue;
+    // The fused inner kernel is a candidate where R fits in shared memory.
     // For a small R (at most 2048 nodes) the fused kernel replaces p-1
     // launches of a few microseconds each; a four-step timing does not tell
     // the two apart reliably there, so only the fused shapes are timed.
     std::vector<int> shapes = {8, 16, 32, 108, 116, 132};
-    if (c->fused_mode >= 1 && !blocks && fused_ok<Real>(c, mg, n_R, S, v, ds.p)) {
+    if (c->fused_mode >= 1 && fused_ok<Real>(c, mg, n_R, S, v, ds.p)) {
       if (n_R <= 2048) shapes.clear();
       for (int k : {8, 16, 32, 108, 116, 132}) shapes.push_back(2000 + k);
     }
     for (int k : shapes) {
       Real* uc = nullptr;
-      int rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, 1, blocks, dts);  // warm
+      int rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, 1, dts);  // warm
       if (!rc) rc = cudaEventRecord(e0, st) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
-      if (!rc) rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, steps, blocks, dts);
+      if (!rc) rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, steps, dts);
       if (!rc) rc = cudaEventRecord(e1, st) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
       if (!rc) rc = cudaEventSynchronize(e1) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
       float ms = 0.f;
@@ -928,7 +817,7 @@ template <typename Real, int KP>
 int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qoi& q,
                  const Field& u0, const Field* v0, const double* d_xi, int64_t S, double* d_Q,
                  double* d_uN, Workspace& ws, cudaStream_t st, std::unique_ptr<SliceTask>* defer,
-                 const RaggedSpec* rg) {
+                 const RaggedSpec* rg, bool allow_graph) {
   const HostMesh& h = mg.h;
   const size_t rb = sizeof(Real);
   const int64_t n_nodes = h.n_nodes;
@@ -969,13 +858,11 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
                                                       Sel<Real>::psi(mg), xi, W,
                                                       rg ? static_cast<const Real*>(rg->d_sig) : nullptr);
     LF_CUDA(c, cudaGetLastError());
-    pr.end(LFLTS_KERNEL_INIT, double(S) * rb * (3.0 * n_nodes + double(h.n_edges)));
+    pr.end(LFLTS_KERNEL_INIT, double(S) * rb * 3.0 * n_nodes);  // u (twice) and d written
     c->launches += 2;  // three kernels in this class
     return 0;
   };
 
-  const MeshGPU::DevBlocks* blocks = nullptr;
-  if (c->force_blocked && !rg) LF_TRY(get_blocks<Real>(c, mg, S, p, blocks));
   int vec = 1, cps = 16;
   if (c->autotune && !mg.tuned.count(std::make_tuple(S, ds.precision, ds.p))) {
     const int64_t l0 = c->launches;
@@ -984,13 +871,12 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
     const int rc = a1();  // edge weights and a valid state for the timing runs
     c->profiling = prof;
     LF_TRY(rc);
-    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks, rg ? rg->d_dts : nullptr));
+    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, rg ? rg->d_dts : nullptr));
     c->tune_launches += c->launches - l0;
     c->launches = l0;
   } else {
-    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks, rg ? rg->d_dts : nullptr));
+    LF_TRY(launch_shape<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, rg ? rg->d_dts : nullptr));
   }
-  if (c->force_blocked && blocks) cps = 1000 + cps % 1000;
 
   // QoI at each draw's final step (Sec. 2.1; FP64 compensated sums), stage 1
   // per finished draw range, stage 2 once; optional gather of u_N.  Captured
@@ -1027,7 +913,7 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   };
   auto body = [&]() -> int {
     LF_TRY(a1());
-    auto loop = make_sliced<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks, rg, lo);
+    auto loop = make_sliced<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, rg, lo);
     LF_TRY(loop->advance(ds.n_steps));
     return loop->finish();
   };
@@ -1037,13 +923,14 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   // (more than kGraphMaxKernels kernels) launch directly: their graphs would
   // take seconds and gigabytes of host memory to build, and their kernels
   // outlast the launch cost anyway.
-  const int64_t inner_per_step = n_R == 0 ? 0 : (cps >= 2000 ? 1 : (cps >= 1000 ? 8 * (p - 1) : p - 1));
+  const int64_t inner_per_step = n_R == 0 ? 0 : (cps >= 2000 ? 1 : p - 1);
   const int64_t est_kernels = ds.n_steps * (1 + inner_per_step);
-  const bool use_graph = c->graphs && !c->profiling && st != nullptr && est_kernels <= kGraphMaxKernels;
+  const bool use_graph =
+      allow_graph && c->graphs && !c->profiling && st != nullptr && est_kernels <= kGraphMaxKernels;
   if (!use_graph) {
     if (!defer) return body();
     LF_TRY(a1());
-    *defer = make_sliced<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, blocks, rg, lo);
+    *defer = make_sliced<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, rg, lo);
     return 0;
   }
   GraphKey key;
@@ -1114,15 +1001,15 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
 template <typename Real>
 int run_solve(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64_t S, double* d_Q,
               double* d_uN, Workspace& ws, cudaStream_t st, std::unique_ptr<SliceTask>* defer,
-              const RaggedSpec* rg) {
+              const RaggedSpec* rg, bool allow_graph) {
   MeshGPU& mg = *c->meshes[ds.mesh_id];
   const Qoi& q = c->qois[ds.qoi_id];
   const Field& u0 = c->fields[ds.u0_field];
   const Field* v0 = ds.v0_field >= 0 ? &c->fields[ds.v0_field] : nullptr;
   switch (mg.h.KP) {
-    case 4: return run_solve_kp<Real, 4>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st, defer, rg);
-    case 8: return run_solve_kp<Real, 8>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st, defer, rg);
-    default: return run_solve_kp<Real, 16>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st, defer, rg);
+    case 4: return run_solve_kp<Real, 4>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st, defer, rg, allow_graph);
+    case 8: return run_solve_kp<Real, 8>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st, defer, rg, allow_graph);
+    default: return run_solve_kp<Real, 16>(c, ds, mg, q, u0, v0, d_xi, S, d_Q, d_uN, ws, st, defer, rg, allow_graph);
   }
 }
 
@@ -1149,11 +1036,12 @@ int check_desc(lflts_ctx* c, const lflts_solve_desc* ds) {
 
 // defer non-null: a solve that is not captured into a graph only queues its
 // start here and returns its time loop as a SliceTask in *defer.
+// allow_graph false: never captured (the time loop of a sliced run).
 int solve_device(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64_t S, double* d_Q,
                  double* d_uN, Workspace& ws, cudaStream_t st, std::unique_ptr<SliceTask>* defer = nullptr,
-                 const RaggedSpec* rg = nullptr) {
-  if (ds.precision == 32) return run_solve<float>(c, ds, d_xi, S, d_Q, d_uN, ws, st, defer, rg);
-  return run_solve<double>(c, ds, d_xi, S, d_Q, d_uN, ws, st, defer, rg);
+                 const RaggedSpec* rg = nullptr, bool allow_graph = true) {
+  if (ds.precision == 32) return run_solve<float>(c, ds, d_xi, S, d_Q, d_uN, ws, st, defer, rg, allow_graph);
+  return run_solve<double>(c, ds, d_xi, S, d_Q, d_uN, ws, st, defer, rg, allow_graph);
 }
 
 Workspace& workspace(lflts_ctx* c, size_t slot) {
@@ -1315,7 +1203,6 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
   int64_t n_edges_R = 0;
   for (int64_t e = 0; e < h.n_edges; ++e) n_edges_R += h.edge_i[e] < n_R;
   const double Srb = double(S) * rb;
-  const double edgeP_bytes = double(h.n_edges_P) * Srb;
   const double edges_bytes = (kF32 ? 8.0 : 16.0) * double(h.n_edges) * S + 2.0 * double(h.n_free) * Srb +
                              double(2 * p - 2) * double(n_R) * Srb;
   const Geo gE32 = geometry(c, std::max<int64_t>(h.n_edges, 1), S / VEC);
@@ -1353,7 +1240,7 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
               stp.md, (int)S, gR.SB, W, cur, s_cur, prv, s_prv, rs + (m - 1) * rn, gs, nullptr, nullptr, nullptr,
               (Real)(1.0 + stp.beta[m]), (Real)stp.beta[m], (Real)stp.cm[m], Real(0), (int)S);
           LF_CUDA(c, cudaGetLastError());
-          pr.end(LFLTS_KERNEL_ADJ_INNER, double(m == 1 ? 2 : (m == 2 ? 3 : 4)) * double(n_R) * Srb + edgeP_bytes);
+          pr.end(LFLTS_KERNEL_ADJ_INNER, double(m == 1 ? 2 : (m == 2 ? 3 : 4)) * double(n_R) * Srb);
         }
         // (iii) inner adjoint rho_{p-1} .. rho_1 (rho_p = kappa nu_{n+1})
         for (int m = p - 1; m >= 1; --m) {
@@ -1367,7 +1254,7 @@ int run_grad(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, int64
                                                            rho + (m - 1) * rn, (Real)(1.0 + stp.beta[m]), b1,
                                                            (Real)stp.cm[m]);
           LF_CUDA(c, cudaGetLastError());
-          pr.end(LFLTS_KERNEL_ADJ_INNER, double(s2p ? 3 : 2) * double(n_R) * Srb + edgeP_bytes);
+          pr.end(LFLTS_KERNEL_ADJ_INNER, double(s2p ? 3 : 2) * double(n_R) * Srb);
         }
       }
       // (iv) edge accumulators
@@ -1443,13 +1330,295 @@ int grad_device(lflts_ctx* c, const lflts_solve_desc& ds, const double* d_xi, in
   return run_grad_kp<double, 1>(c, ds, d_xi, S, k_ck, d_Q, d_G, st);
 }
 
+// ---------------------------------------------------------------------------
+// MLMC level pairs (lflts_run_pairs, lflts_run_pairs_slice).  Solves that
+// differ at most in (dt, n_steps) share a batch (a group): identical ones
+// form a segment, and a group with several segments is ragged (each draw
+// steps with its own dt for its own count; segments sorted by step count).
+// ---------------------------------------------------------------------------
+struct PairMember {
+  int job;
+  bool fine;
+  int64_t off;
+};
+struct PairSeg {
+  lflts_solve_desc desc;
+  int64_t S = 0;
+  std::vector<PairMember> members;
+};
+struct PairGroup {
+  std::vector<PairSeg> segs;
+  int64_t S = 0;
+};
+struct PairRun {
+  uint64_t sig = 0;
+  int next = 0, n_slices = 1;
+  std::vector<PairGroup> groups;
+  std::vector<RaggedSpec> specs;
+  std::vector<std::unique_ptr<SliceTask>> tasks;  // null: the group's whole solve is queued (a graph)
+  std::vector<cudaStream_t> gst;                  // stream of each group
+  std::vector<int64_t> N;                         // outer steps of each group's time loop
+};
+
+// FNV-1a over the jobs' bytes, the memory kind and the slice count: the
+// calls of one sliced run must pass the same jobs.
+uint64_t jobs_signature(const lflts_pair_job* jobs, int n_jobs, int mem, int n_slices) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t k = 0; k < n; ++k) h = (h ^ b[k]) * 1099511628211ull;
+  };
+  if (jobs)
+    for (int j = 0; j < n_jobs; ++j) {
+      const lflts_pair_job& jb = jobs[j];
+      for (const lflts_solve_desc* d : {&jb.fine, &jb.coarse}) {
+        mix(&d->mesh_id, sizeof(int) * 6);
+        mix(&d->nu, sizeof(double) * 2);
+        mix(&d->n_steps, sizeof(int64_t));
+        mix(&d->source_id, sizeof(int));
+        mix(&d->src_f0, sizeof(double) * 3);
+      }
+      mix(&jb.has_coarse, sizeof(int));
+      mix(&jb.xi, sizeof(void*));
+      mix(&jb.S, sizeof(int64_t));
+      mix(&jb.dQ, sizeof(void*) * 3);
+    }
+  mix(&mem, sizeof(int));
+  mix(&n_slices, sizeof(int));
+  return h;
+}
+
+// Validate and group the jobs, copy the draws of every group into its
+// workspace and queue the start of each group's solve (coefficients, start
+// values); the time loops stay in run.tasks unless a whole solve went into a
+// graph (n_slices == 1 only).
+int pairs_start(lflts_ctx* c, PairRun& run, const lflts_pair_job* jobs, int n_jobs, int mem, int n_slices,
+                cudaStream_t st) {
+  run.n_slices = n_slices;
+  std::vector<PairGroup>& groups = run.groups;
+  auto same_batch = [](const lflts_solve_desc& a, const lflts_solve_desc& b) {
+    return a.mesh_id == b.mesh_id && a.qoi_id == b.qoi_id && a.u0_field == b.u0_field &&
+           a.v0_field == b.v0_field && a.precision == b.precision && a.p == b.p && a.nu == b.nu &&
+           a.source_id == b.source_id && a.src_f0 == b.src_f0 && a.src_t0 == b.src_t0 && a.src_amp == b.src_amp;
+  };
+  auto add_member = [&](const lflts_solve_desc& ds, int j, bool fine, int64_t S) {
+    PairGroup* gp = nullptr;
+    for (auto& gr : groups)
+      if (same_batch(gr.segs[0].desc, ds)) gp = &gr;
+    if (!gp) {
+      groups.emplace_back();
+      gp = &groups.back();
+    }
+    PairSeg* sp = nullptr;
+    for (auto& sg : gp->segs)
+      if (sg.desc.dt == ds.dt && sg.desc.n_steps == ds.n_steps) sp = &sg;
+    if (!sp) {
+      gp->segs.emplace_back();
+      sp = &gp->segs.back();
+      sp->desc = ds;
+    }
+    sp->members.push_back({j, fine, sp->S});
+    sp->S += S;
+    gp->S += S;
+  };
+  for (int j = 0; j < n_jobs; ++j) {
+    const lflts_pair_job& jb = jobs[j];
+    if (!jb.xi || !jb.dQ || jb.S < 1)
+      return fail(c, LFLTS_ERR_ARG, "run_pairs: job " + std::to_string(j) + " has null xi/dQ or S < 1");
+    LF_TRY(check_desc(c, &jb.fine));
+    if (jb.has_coarse) {
+      LF_TRY(check_desc(c, &jb.coarse));
+      if (c->meshes[jb.coarse.mesh_id]->h.K != c->meshes[jb.fine.mesh_id]->h.K)
+        return fail(c, LFLTS_ERR_ARG, "run_pairs: fine and coarse meshes have different K");
+    }
+    add_member(jb.fine, j, true, jb.S);
+    if (jb.has_coarse) add_member(jb.coarse, j, false, jb.S);
+  }
+  for (auto& gr : groups)
+    if (gr.S > kMaxS) return fail(c, LFLTS_ERR_ARG, "run_pairs: merged batch larger than 2097120 samples");
+  // segments by step count (descending), members' offsets within the batch
+  std::vector<RaggedSpec>& specs = run.specs;
+  specs.assign(groups.size(), RaggedSpec());
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    PairGroup& gr = groups[gi];
+    std::stable_sort(gr.segs.begin(), gr.segs.end(),
+                     [](const PairSeg& a, const PairSeg& b) { return a.desc.n_steps > b.desc.n_steps; });
+    int64_t off = 0;
+    uint64_t hsh = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+      for (int b = 0; b < 8; ++b) hsh = (hsh ^ ((v >> (8 * b)) & 0xff)) * 1099511628211ull;
+    };
+    for (PairSeg& sg : gr.segs) {
+      for (PairMember& mb : sg.members) mb.off += off;
+      specs[gi].segs.push_back({off, sg.S, sg.desc.n_steps, sg.desc.dt});
+      uint64_t dbits = 0;
+      std::memcpy(&dbits, &sg.desc.dt, sizeof(dbits));
+      mix(uint64_t(sg.desc.n_steps));
+      mix(uint64_t(sg.S));
+      mix(dbits);
+      off += sg.S;
+    }
+    specs[gi].hash = hsh;
+  }
+
+  // ---- streams and events ----------------------------------------------------
+  const size_t ng = groups.size();
+  while (c->streams.size() < ng) {
+    cudaStream_t s;
+    LF_CUDA(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    c->streams.push_back(s);
+  }
+  while (c->sync_events.size() < ng + 1) {
+    cudaEvent_t e;
+    LF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->sync_events.push_back(e);
+  }
+  LF_TRY(reset_bad(c, st));
+  LF_CUDA(c, cudaEventRecord(c->sync_events[ng], st));
+
+  // ---- per group: gather xi, queue the start of the solve -----------------------
+  // With per-launch profiling on, every group runs on the caller's stream, one
+  // after the other, so that each kernel's event times are its own.
+  run.tasks.resize(ng);
+  run.gst.assign(ng, st);
+  run.N.assign(ng, 0);
+  for (size_t gi = 0; gi < ng; ++gi) {
+    PairGroup& gr = groups[gi];
+    Workspace& ws = workspace(c, 1 + gi);
+    const lflts_solve_desc& gd = gr.segs[0].desc;  // the longest segment: dt_ref and the step count
+    run.N[gi] = gd.n_steps;
+    const int K = c->meshes[gd.mesh_id]->h.K;
+    cudaStream_t gs = c->profiling ? st : c->streams[gi];
+    run.gst[gi] = gs;
+    LF_CUDA(c, cudaStreamWaitEvent(gs, c->sync_events[ng], 0));
+    LF_TRY(ensure(c, ws.xraw, size_t(gr.S) * K * sizeof(double)));
+    LF_TRY(ensure(c, ws.Q, size_t(gr.S) * sizeof(double)));
+    for (const PairSeg& sg : gr.segs)
+      for (const PairMember& mb : sg.members) {
+        const lflts_pair_job& jb = jobs[mb.job];
+        LF_CUDA(c, cudaMemcpyAsync(static_cast<double*>(ws.xraw.p) + mb.off * K, jb.xi,
+                                   size_t(jb.S) * K * sizeof(double),
+                                   mem == LFLTS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, gs));
+      }
+    const RaggedSpec* rg = nullptr;
+    if (gr.segs.size() > 1) {  // per-draw dt and weight scale of the ragged batch
+      const size_t rb = gd.precision == 32 ? sizeof(float) : sizeof(double);
+      ws.h_dts.assign(size_t(gr.S), 0.0);
+      ws.h_sig.assign(size_t(gr.S) * rb, 0);
+      for (const RaggedSeg& sg : specs[gi].segs)
+        for (int64_t k = 0; k < sg.cnt; ++k) {
+          const double sc = (sg.dt / gd.dt) * (sg.dt / gd.dt);
+          ws.h_dts[size_t(sg.off + k)] = sg.dt;
+          if (rb == sizeof(float)) {
+            const float f = float(sc);
+            std::memcpy(ws.h_sig.data() + size_t(sg.off + k) * rb, &f, rb);
+          } else {
+            std::memcpy(ws.h_sig.data() + size_t(sg.off + k) * rb, &sc, rb);
+          }
+        }
+      LF_TRY(ensure(c, ws.dts, size_t(gr.S) * sizeof(double)));
+      LF_TRY(ensure(c, ws.sig, size_t(gr.S) * rb));
+      LF_CUDA(c, cudaMemcpyAsync(ws.dts.p, ws.h_dts.data(), size_t(gr.S) * sizeof(double), cudaMemcpyHostToDevice, gs));
+      LF_CUDA(c, cudaMemcpyAsync(ws.sig.p, ws.h_sig.data(), size_t(gr.S) * rb, cudaMemcpyHostToDevice, gs));
+      specs[gi].d_dts = static_cast<const double*>(ws.dts.p);
+      specs[gi].d_sig = ws.sig.p;
+      rg = &specs[gi];
+    }
+    LF_TRY(solve_device(c, gd, static_cast<double*>(ws.xraw.p), gr.S, static_cast<double*>(ws.Q.p), nullptr, ws,
+                        gs, &run.tasks[gi], rg, n_slices == 1));
+  }
+  return 0;
+}
+
+// Queue slice k of every group's time loop: outer steps
+// [floor(N k / n), floor(N (k+1) / n)), in turns of kSliceSteps steps group
+// after group so that every stream keeps work queued; the last slice also
+// queues the QoI.  The caller's stream then waits for every group.
+int pairs_advance(lflts_ctx* c, PairRun& run, int slice, cudaStream_t st) {
+  const size_t ng = run.groups.size();
+  std::vector<int64_t> target(ng, 0);
+  for (size_t gi = 0; gi < ng; ++gi) target[gi] = run.N[gi] * (slice + 1) / run.n_slices;
+  for (bool more = true; more;) {
+    more = false;
+    for (size_t gi = 0; gi < ng; ++gi) {
+      SliceTask* t = run.tasks[gi].get();
+      if (!t) continue;
+      const int64_t left = target[gi] - t->position();
+      if (left <= 0) continue;
+      LF_TRY(t->advance(std::min<int64_t>(left, kSliceSteps)));
+      more = more || target[gi] - t->position() > 0;
+    }
+  }
+  const bool last = slice + 1 == run.n_slices;
+  for (size_t gi = 0; gi < ng; ++gi) {
+    if (last && run.tasks[gi]) LF_TRY(run.tasks[gi]->finish());
+    LF_CUDA(c, cudaEventRecord(c->sync_events[gi], run.gst[gi]));
+  }
+  for (size_t gi = 0; gi < ng; ++gi) LF_CUDA(c, cudaStreamWaitEvent(st, c->sync_events[gi], 0));
+  return 0;
+}
+
+// After the last slice: per job dQ, Qf and the level sums on the caller's
+// stream (and the copies to host memory).
+int pairs_finish(lflts_ctx* c, PairRun& run, const lflts_pair_job* jobs, int n_jobs, int mem, cudaStream_t st) {
+  const size_t ng = run.groups.size();
+  Workspace& ws0 = workspace(c, 0);
+  int64_t total = 0;
+  for (int j = 0; j < n_jobs; ++j) total += jobs[j].S;
+  if (mem == LFLTS_MEM_HOST) LF_TRY(ensure(c, ws0.Q, size_t(total) * 2 * sizeof(double) + 4 * sizeof(double) * n_jobs));
+  int64_t hoff = 0;
+  for (int j = 0; j < n_jobs; ++j) {
+    const lflts_pair_job& jb = jobs[j];
+    const double* qf = nullptr;
+    const double* qc = nullptr;
+    for (size_t gi = 0; gi < ng; ++gi)
+      for (const PairSeg& sg : run.groups[gi].segs)
+        for (const PairMember& mb : sg.members)
+          if (mb.job == j) {
+            const double* base = static_cast<double*>(workspace(c, 1 + gi).Q.p) + mb.off;
+            if (mb.fine) qf = base;
+            else qc = base;
+          }
+    double* dq_dst = jb.dQ;
+    double* qf_dst = jb.Qf;
+    double* sums_dst = jb.sums;
+    if (mem == LFLTS_MEM_HOST) {
+      double* base = static_cast<double*>(ws0.Q.p);
+      dq_dst = base + hoff;
+      qf_dst = base + total + hoff;
+      sums_dst = base + 2 * total + 4 * j;
+    }
+    {
+      Prof pr(c, st);
+      k_pair_diff<<<blocks_for(jb.S, 128, 1 << 20), 128, 0, st>>>((int)jb.S, qf, qc, dq_dst, qf_dst);
+      LF_CUDA(c, cudaGetLastError());
+      k_level_sums<<<1, 256, 0, st>>>(jb.S, qf, qc, sums_dst);
+      LF_CUDA(c, cudaGetLastError());
+      pr.end(LFLTS_KERNEL_SUMS, double(jb.S) * 8.0 * (qc ? 5.0 : 3.0));
+      c->launches++;
+    }
+    if (mem == LFLTS_MEM_HOST) {
+      LF_CUDA(c, cudaMemcpyAsync(jb.dQ, dq_dst, size_t(jb.S) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      if (jb.Qf) LF_CUDA(c, cudaMemcpyAsync(jb.Qf, qf_dst, size_t(jb.S) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      if (jb.sums) LF_CUDA(c, cudaMemcpyAsync(jb.sums, sums_dst, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    hoff += jb.S;
+  }
+  if (mem == LFLTS_MEM_HOST) return check_bad(c, st);
+  return LFLTS_OK;
+}
+
 }  // namespace
+
+lflts_ctx::~lflts_ctx() = default;
 
 // Error reporting for entry points defined in other translation units.
 int lflts_internal_set_error(lflts_ctx* ctx, int code, const char* msg) {
   if (ctx) ctx->err = msg ? msg : "";
   return code;
 }
+
+int lflts_internal_ctx_device(const lflts_ctx* ctx) { return ctx ? ctx->device : -1; }
 
 // ============================================================================
 // ABI
@@ -1741,211 +1910,50 @@ int lflts_level_sums(lflts_ctx* c, const double* Qf, const double* Qc, int64_t S
 }
 
 int lflts_run_pairs(lflts_ctx* c, const lflts_pair_job* jobs, int n_jobs, int mem, void* stream) {
+  return lflts_run_pairs_slice(c, jobs, n_jobs, mem, 0, 1, stream);
+}
+
+int lflts_run_pairs_slice(lflts_ctx* c, const lflts_pair_job* jobs, int n_jobs, int mem, int slice, int n_slices,
+                          void* stream) {
   if (!c) return LFLTS_ERR_ARG;
   c->err.clear();
   LF_TRY(set_device(c));
-  if (!jobs || n_jobs < 1) return fail(c, LFLTS_ERR_ARG, "run_pairs: no jobs");
-  if (mem != LFLTS_MEM_HOST && mem != LFLTS_MEM_DEVICE) return fail(c, LFLTS_ERR_ARG, "run_pairs: bad mem kind");
+  if (!jobs || n_jobs < 1 || (mem != LFLTS_MEM_HOST && mem != LFLTS_MEM_DEVICE)) {
+    c->run.reset();
+    return fail(c, LFLTS_ERR_ARG, "run_pairs: no jobs or bad mem kind");
+  }
+  if (n_slices < 1 || slice < 0 || slice >= n_slices) {
+    c->run.reset();
+    return fail(c, LFLTS_ERR_ARG, "run_pairs_slice: need 0 <= slice < n_slices");
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-
-  // ---- group the solves ------------------------------------------------------
-  // Solves that differ at most in (dt, n_steps) share a batch: identical ones
-  // form a segment, and a batch with several segments is ragged (each draw
-  // steps with its own dt for its own count; segments sorted by step count).
-  struct Member { int job; bool fine; int64_t off; };
-  struct Seg { lflts_solve_desc desc; int64_t S = 0; std::vector<Member> members; };
-  struct Group { std::vector<Seg> segs; int64_t S = 0; };
-  std::vector<Group> groups;
-  auto same_batch = [](const lflts_solve_desc& a, const lflts_solve_desc& b) {
-    return a.mesh_id == b.mesh_id && a.qoi_id == b.qoi_id && a.u0_field == b.u0_field &&
-           a.v0_field == b.v0_field && a.precision == b.precision && a.p == b.p && a.nu == b.nu &&
-           a.source_id == b.source_id && a.src_f0 == b.src_f0 && a.src_t0 == b.src_t0 && a.src_amp == b.src_amp;
-  };
-  auto add_member = [&](const lflts_solve_desc& ds, int j, bool fine, int64_t S) {
-    Group* gp = nullptr;
-    for (auto& gr : groups)
-      if (same_batch(gr.segs[0].desc, ds)) gp = &gr;
-    if (!gp) {
-      groups.emplace_back();
-      gp = &groups.back();
-    }
-    Seg* sp = nullptr;
-    for (auto& sg : gp->segs)
-      if (sg.desc.dt == ds.dt && sg.desc.n_steps == ds.n_steps) sp = &sg;
-    if (!sp) {
-      gp->segs.emplace_back();
-      sp = &gp->segs.back();
-      sp->desc = ds;
-    }
-    sp->members.push_back({j, fine, sp->S});
-    sp->S += S;
-    gp->S += S;
-  };
-  for (int j = 0; j < n_jobs; ++j) {
-    const lflts_pair_job& jb = jobs[j];
-    if (!jb.xi || !jb.dQ || jb.S < 1) return fail(c, LFLTS_ERR_ARG, "run_pairs: job " + std::to_string(j) + " has null xi/dQ or S < 1");
-    LF_TRY(check_desc(c, &jb.fine));
-    if (jb.has_coarse) {
-      LF_TRY(check_desc(c, &jb.coarse));
-      if (c->meshes[jb.coarse.mesh_id]->h.K != c->meshes[jb.fine.mesh_id]->h.K)
-        return fail(c, LFLTS_ERR_ARG, "run_pairs: fine and coarse meshes have different K");
-    }
-    add_member(jb.fine, j, true, jb.S);
-    if (jb.has_coarse) add_member(jb.coarse, j, false, jb.S);
+  const uint64_t sig = jobs_signature(jobs, n_jobs, mem, n_slices);
+  if (slice == 0) {
+    c->run.reset();  // a new run replaces one left unfinished
+    std::unique_ptr<PairRun> run(new PairRun());
+    LF_TRY(pairs_start(c, *run, jobs, n_jobs, mem, n_slices, st));
+    run->sig = sig;
+    c->run = std::move(run);
+  } else if (!c->run || c->run->sig != sig || c->run->next != slice) {
+    c->run.reset();
+    return fail(c, LFLTS_ERR_ARG,
+                "run_pairs_slice: slice " + std::to_string(slice) +
+                    " does not continue the run in progress (same jobs, memory kind and n_slices, slices in order)");
   }
-  for (auto& gr : groups)
-    if (gr.S > kMaxS) return fail(c, LFLTS_ERR_ARG, "run_pairs: merged batch larger than 2097120 samples");
-  // segments by step count (descending), members' offsets within the batch
-  std::vector<RaggedSpec> specs(groups.size());
-  for (size_t gi = 0; gi < groups.size(); ++gi) {
-    Group& gr = groups[gi];
-    std::stable_sort(gr.segs.begin(), gr.segs.end(),
-                     [](const Seg& a, const Seg& b) { return a.desc.n_steps > b.desc.n_steps; });
-    int64_t off = 0;
-    uint64_t hsh = 1469598103934665603ull;
-    auto mix = [&](uint64_t v) {
-      for (int b = 0; b < 8; ++b) hsh = (hsh ^ ((v >> (8 * b)) & 0xff)) * 1099511628211ull;
-    };
-    for (Seg& sg : gr.segs) {
-      for (Member& mb : sg.members) mb.off += off;
-      specs[gi].segs.push_back({off, sg.S, sg.desc.n_steps, sg.desc.dt});
-      uint64_t dbits = 0;
-      std::memcpy(&dbits, &sg.desc.dt, sizeof(dbits));
-      mix(uint64_t(sg.desc.n_steps));
-      mix(uint64_t(sg.S));
-      mix(dbits);
-      off += sg.S;
-    }
-    specs[gi].hash = hsh;
+  PairRun& run = *c->run;
+  const int rc = pairs_advance(c, run, slice, st);
+  if (rc) {
+    c->run.reset();
+    return rc;
   }
-
-  // ---- streams and events ----------------------------------------------------
-  const size_t ng = groups.size();
-  while (c->streams.size() < ng) {
-    cudaStream_t s;
-    LF_CUDA(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    c->streams.push_back(s);
+  run.next = slice + 1;
+  if (slice + 1 < n_slices) {
+    if (mem == LFLTS_MEM_HOST) LF_CUDA(c, cudaStreamSynchronize(st));
+    return LFLTS_OK;
   }
-  while (c->sync_events.size() < ng + 1) {
-    cudaEvent_t e;
-    LF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    c->sync_events.push_back(e);
-  }
-  LF_TRY(reset_bad(c, st));
-  LF_CUDA(c, cudaEventRecord(c->sync_events[ng], st));
-
-  // ---- per group: gather xi, solve ------------------------------------------
-  // Groups captured into graphs are queued whole; the time loops of the
-  // others are queued in slices of kSliceSteps outer steps, group after
-  // group, so that every stream keeps work queued.  With per-launch
-  // profiling on, every group is queued whole (its kernels then rarely share
-  // the GPU with another group's, so their event times stay their own).
-  std::vector<std::unique_ptr<SliceTask>> tasks(ng);
-  const bool slice = !c->profiling;
-  for (size_t gi = 0; gi < ng; ++gi) {
-    Group& gr = groups[gi];
-    Workspace& ws = workspace(c, 1 + gi);
-    const lflts_solve_desc& gd = gr.segs[0].desc;  // the longest segment: dt_ref and the step count
-    const int K = c->meshes[gd.mesh_id]->h.K;
-    cudaStream_t gs = c->streams[gi];
-    LF_CUDA(c, cudaStreamWaitEvent(gs, c->sync_events[ng], 0));
-    LF_TRY(ensure(c, ws.xraw, size_t(gr.S) * K * sizeof(double)));
-    LF_TRY(ensure(c, ws.Q, size_t(gr.S) * sizeof(double)));
-    for (const Seg& sg : gr.segs)
-      for (const Member& mb : sg.members) {
-        const lflts_pair_job& jb = jobs[mb.job];
-        LF_CUDA(c, cudaMemcpyAsync(static_cast<double*>(ws.xraw.p) + mb.off * K, jb.xi,
-                                   size_t(jb.S) * K * sizeof(double),
-                                   mem == LFLTS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, gs));
-      }
-    const RaggedSpec* rg = nullptr;
-    if (gr.segs.size() > 1) {  // per-draw dt and weight scale of the ragged batch
-      const size_t rb = gd.precision == 32 ? sizeof(float) : sizeof(double);
-      ws.h_dts.assign(size_t(gr.S), 0.0);
-      ws.h_sig.assign(size_t(gr.S) * rb, 0);
-      for (const RaggedSeg& sg : specs[gi].segs)
-        for (int64_t k = 0; k < sg.cnt; ++k) {
-          const double sc = (sg.dt / gd.dt) * (sg.dt / gd.dt);
-          ws.h_dts[size_t(sg.off + k)] = sg.dt;
-          if (rb == sizeof(float)) {
-            const float f = float(sc);
-            std::memcpy(ws.h_sig.data() + size_t(sg.off + k) * rb, &f, rb);
-          } else {
-            std::memcpy(ws.h_sig.data() + size_t(sg.off + k) * rb, &sc, rb);
-          }
-        }
-      LF_TRY(ensure(c, ws.dts, size_t(gr.S) * sizeof(double)));
-      LF_TRY(ensure(c, ws.sig, size_t(gr.S) * rb));
-      LF_CUDA(c, cudaMemcpyAsync(ws.dts.p, ws.h_dts.data(), size_t(gr.S) * sizeof(double), cudaMemcpyHostToDevice, gs));
-      LF_CUDA(c, cudaMemcpyAsync(ws.sig.p, ws.h_sig.data(), size_t(gr.S) * rb, cudaMemcpyHostToDevice, gs));
-      specs[gi].d_dts = static_cast<const double*>(ws.dts.p);
-      specs[gi].d_sig = ws.sig.p;
-      rg = &specs[gi];
-    }
-    LF_TRY(solve_device(c, gd, static_cast<double*>(ws.xraw.p), gr.S, static_cast<double*>(ws.Q.p), nullptr, ws,
-                        gs, slice ? &tasks[gi] : nullptr, rg));
-    if (!tasks[gi]) LF_CUDA(c, cudaEventRecord(c->sync_events[gi], gs));
-  }
-  for (bool more = true; more;) {
-    more = false;
-    for (size_t gi = 0; gi < ng; ++gi)
-      if (tasks[gi] && !tasks[gi]->done()) {
-        LF_TRY(tasks[gi]->advance(kSliceSteps));
-        more = more || !tasks[gi]->done();
-      }
-  }
-  for (size_t gi = 0; gi < ng; ++gi)
-    if (tasks[gi]) {
-      LF_TRY(tasks[gi]->finish());
-      LF_CUDA(c, cudaEventRecord(c->sync_events[gi], c->streams[gi]));
-    }
-  for (size_t gi = 0; gi < ng; ++gi) LF_CUDA(c, cudaStreamWaitEvent(st, c->sync_events[gi], 0));
-
-  // ---- per job: dQ, Qf and level sums on the caller's stream ----------------
-  Workspace& ws0 = workspace(c, 0);
-  int64_t total = 0;
-  for (int j = 0; j < n_jobs; ++j) total += jobs[j].S;
-  if (mem == LFLTS_MEM_HOST) LF_TRY(ensure(c, ws0.Q, size_t(total) * 2 * sizeof(double) + 4 * sizeof(double) * n_jobs));
-  int64_t hoff = 0;
-  for (int j = 0; j < n_jobs; ++j) {
-    const lflts_pair_job& jb = jobs[j];
-    const double* qf = nullptr;
-    const double* qc = nullptr;
-    for (size_t gi = 0; gi < ng; ++gi)
-      for (const Seg& sg : groups[gi].segs)
-        for (const Member& mb : sg.members)
-          if (mb.job == j) {
-            const double* base = static_cast<double*>(workspace(c, 1 + gi).Q.p) + mb.off;
-            if (mb.fine) qf = base;
-            else qc = base;
-          }
-    double* dq_dst = jb.dQ;
-    double* qf_dst = jb.Qf;
-    double* sums_dst = jb.sums;
-    if (mem == LFLTS_MEM_HOST) {
-      double* base = static_cast<double*>(ws0.Q.p);
-      dq_dst = base + hoff;
-      qf_dst = base + total + hoff;
-      sums_dst = base + 2 * total + 4 * j;
-    }
-    {
-      Prof pr(c, st);
-      k_pair_diff<<<blocks_for(jb.S, 128, 1 << 20), 128, 0, st>>>((int)jb.S, qf, qc, dq_dst, qf_dst);
-      LF_CUDA(c, cudaGetLastError());
-      k_level_sums<<<1, 256, 0, st>>>(jb.S, qf, qc, sums_dst);
-      LF_CUDA(c, cudaGetLastError());
-      pr.end(LFLTS_KERNEL_SUMS, double(jb.S) * 8.0 * (qc ? 5.0 : 3.0));
-      c->launches++;
-    }
-    if (mem == LFLTS_MEM_HOST) {
-      LF_CUDA(c, cudaMemcpyAsync(jb.dQ, dq_dst, size_t(jb.S) * sizeof(double), cudaMemcpyDeviceToHost, st));
-      if (jb.Qf) LF_CUDA(c, cudaMemcpyAsync(jb.Qf, qf_dst, size_t(jb.S) * sizeof(double), cudaMemcpyDeviceToHost, st));
-      if (jb.sums) LF_CUDA(c, cudaMemcpyAsync(jb.sums, sums_dst, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    }
-    hoff += jb.S;
-  }
-  if (mem == LFLTS_MEM_HOST) return check_bad(c, st);
-  return LFLTS_OK;
+  const int rf = pairs_finish(c, run, jobs, n_jobs, mem, st);
+  c->run.reset();
+  return rf;
 }
 
 int lflts_grad_xi(lflts_ctx* c, const lflts_solve_desc* ds, const double* xi, int64_t S, int ckpt_every,
@@ -2024,12 +2032,6 @@ int lflts_set_option(lflts_ctx* c, int option, int64_t value) {
   switch (option) {
     case LFLTS_OPT_GRAPHS: c->graphs = value != 0; return LFLTS_OK;
     case LFLTS_OPT_AUTOTUNE: c->autotune = value != 0; return LFLTS_OK;
-    case LFLTS_OPT_BLOCKED: c->force_blocked = value != 0; return LFLTS_OK;
-    case LFLTS_OPT_BLOCK_BUDGET:
-      if (value < 1024) return fail(c, LFLTS_ERR_ARG, "set_option: block budget below 1024 bytes");
-      c->block_budget = double(value);
-      for (auto& m : c->meshes) m->blocks.clear();  // device lists stay owned by the context
-      return LFLTS_OK;
     case LFLTS_OPT_FUSED_INNER:
       if (value < 0 || value > 2) return fail(c, LFLTS_ERR_ARG, "set_option: fused inner mode must be 0, 1 or 2");
       c->fused_mode = static_cast<int>(value);

@@ -3,11 +3,12 @@
 // The regular path (lflts_solve) keeps its QoI partial sums in workspace
 // buffers that the context allocates with cudaMalloc.  Some callers cannot
 // let a library allocate: applications whose device memory is owned by their
-// own pool allocator, code that must not allocate after start-up, or work
-// being recorded into a CUDA graph, where cudaMalloc is not allowed.  This
-// entry point runs the same two-stage compensated reduction with its partial
-// sums in a fixed-size array that lives in the library's device image, so the
-// call itself performs no allocation.
+// own pool allocator (a library cudaMalloc would fragment or exceed its
+// budget), or code that must not allocate once it is running (fixed memory
+// plans, latency-bound loops where a cudaMalloc would synchronise the device).
+// This entry point runs the same two-stage compensated reduction with its
+// partial sums in a fixed-size array that lives in the library's device
+// image, so the call itself performs no allocation.
 //
 // The array below is part of the module: every GPU that loads the library
 // holds it (2 MiB) until the process exits.  All calls on a device share it.
@@ -58,7 +59,7 @@ __global__ void k_qoi_partial_noalloc(const Real* __restrict__ u, int64_t n_rows
   for (int k = k0; k < k1; ++k) {
     const int r = idx[k];
     if (r < 0 || r >= n_rows) continue;  // out-of-range rows are skipped, never read
-    acc.add(gw[k] * (double)u[(size_t)r * S + s]);
+    acc.add(__dmul_rn(gw[k], (double)u[(size_t)r * S + s]));  // rounded alone, as in lflts_solve
   }
   ps[(size_t)c * S + s] = acc.s;
   pc[(size_t)c * S + s] = acc.c;
@@ -78,8 +79,10 @@ __global__ void k_qoi_final_noalloc(int n_chunks, int S, const double* __restric
 
 }  // namespace
 
-// Defined in lflts.cu: stores a message in the context (ctx may be NULL).
+// Defined in lflts.cu: stores a message in the context (ctx may be NULL);
+// the device of a context (-1 for a host-only context).
 int lflts_internal_set_error(lflts_ctx* ctx, int code, const char* msg);
+int lflts_internal_ctx_device(const lflts_ctx* ctx);
 
 extern "C" int lflts_qoi_reduce_noalloc(lflts_ctx* ctx, const void* u, int precision, int64_t n_rows,
                                         int64_t S, const int32_t* idx, const double* g, int64_t nnz,
@@ -95,6 +98,10 @@ extern "C" int lflts_qoi_reduce_noalloc(lflts_ctx* ctx, const void* u, int preci
         ("qoi_reduce_noalloc: ceil(nnz/512) * S = " + std::to_string(n_chunks * S) +
          " exceeds the fixed scratch capacity of " + std::to_string(kScratchDoubles / 2) + " partial sums")
             .c_str());
+  // the context's device when there is one, else the current device
+  const int cdev = ctx ? lflts_internal_ctx_device(ctx) : -1;
+  if (cdev >= 0 && cudaSetDevice(cdev) != cudaSuccess)
+    return lflts_internal_set_error(ctx, LFLTS_ERR_CUDA, "qoi_reduce_noalloc: cannot select the context's device");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)

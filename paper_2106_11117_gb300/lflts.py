@@ -38,12 +38,10 @@ EXPORTED = [
     "lflts_qoi_add", "lflts_solve", "lflts_level_sums", "lflts_run_pairs",
     "lflts_profile_enable", "lflts_profile_reset", "lflts_profile_read", "lflts_launch_count",
     "lflts_qoi_reduce_noalloc", "lflts_grad_xi", "lflts_set_option", "lflts_get_stats",
-    "lflts_source_add", "lflts_interp_weights",
+    "lflts_source_add", "lflts_interp_weights", "lflts_run_pairs_slice",
 ]
 LFLTS_OPT_GRAPHS = 1
 LFLTS_OPT_AUTOTUNE = 2
-LFLTS_OPT_BLOCKED = 3
-LFLTS_OPT_BLOCK_BUDGET = 4
 LFLTS_OPT_FUSED_INNER = 5
 
 
@@ -110,6 +108,7 @@ def load(path: str | None = None):
         "lflts_solve": (i32, [vp, C.POINTER(SolveDesc), vp, i64, vp, vp, i32, vp]),
         "lflts_level_sums": (i32, [vp, vp, vp, i64, vp, i32, vp]),
         "lflts_run_pairs": (i32, [vp, C.POINTER(PairJob), i32, i32, vp]),
+        "lflts_run_pairs_slice": (i32, [vp, C.POINTER(PairJob), i32, i32, i32, i32, vp]),
         "lflts_profile_enable": (i32, [vp, i32]),
         "lflts_profile_reset": (i32, [vp]),
         "lflts_profile_read": (i32, [vp, i32, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -268,6 +267,15 @@ def lflts_level_sums(ctx, Qf, Qc, S, sums, mem=LFLTS_MEM_HOST, stream=None):
 def lflts_run_pairs(ctx, jobs, mem=LFLTS_MEM_HOST, stream=None):
     arr = (PairJob * len(jobs))(*jobs)
     return _check(ctx, load().lflts_run_pairs(ctx, arr, len(jobs), int(mem), stream))
+
+
+def lflts_run_pairs_slice(ctx, jobs, slice, n_slices, mem=LFLTS_MEM_HOST, stream=None):
+    """Slice ``slice`` of ``n_slices`` of the level-pair run of ``jobs``.  The
+    caller keeps one ``(PairJob * n)`` array (or list) and every buffer the jobs
+    point to alive for the whole run."""
+    arr = jobs if isinstance(jobs, C.Array) else (PairJob * len(jobs))(*jobs)
+    return _check(ctx, load().lflts_run_pairs_slice(ctx, arr, len(arr), int(mem), int(slice), int(n_slices),
+                                                    stream))
 
 
 def lflts_profile_enable(ctx, on=True):

@@ -25,11 +25,11 @@ def test_roofline_record_of_the_dominant_class():
     prof = {"coarse": {"launches": 10, "ms": 20.0, "alg_bytes": 100e9},
             "inner": {"launches": 70, "ms": 60.0, "alg_bytes": 360e9},
             "qoi": {"launches": 1, "ms": 0.1, "alg_bytes": 1e6}}
-    r = bench._roofline(prof, ("coarse", "inner"), {"coarse": "k_coarse", "inner": "k_inner"}, 1.05)
+    r = bench._roofline(prof, ("coarse", "inner"), {"coarse": "k_coarse", "inner": "k_inner"})
     assert r["kernel"] == "k_inner"
     assert r["achieved"] == round(360e9 / 0.060 / 1e9, 1)
     assert r["frac"] == round(r["achieved"] / r["peak"], 4)
-    assert abs(r["traffic"] - 1.05 * 360e9 / 70) < 1.0
+    assert r["alg_bytes_per_launch"] == 360e9 / 70
     assert abs(r["share_of_kernel_time"] - round(60.0 / 80.1, 4)) < 1e-12
     j = bench._classes_json(prof)
     assert j["inner"]["alg_GBps"] == round(360e9 / 0.060 / 1e9, 1)
@@ -46,3 +46,13 @@ def test_oracle_work_count_matches_the_metric():
     free = ~m.dirichlet.astype(bool)
     assert units > lev["n_steps"] * int(free.sum())
     assert units < lev["n_steps"] * (1 + cfg.p) * int(free.sum())
+
+
+def test_slices_cover_every_outer_step_once():
+    """The bench step is one time slice; n consecutive slices run every outer
+    step of a batch exactly once (the library's floor(N k / n) rule)."""
+    for N in (1, 7, 432, 1727, 6907):
+        for n in (1, 3, 20, 64):
+            st = bench.slice_steps(N, n)
+            assert sum(st) == N and len(st) == n
+            assert max(st) - min(st) <= 1

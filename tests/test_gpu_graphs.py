@@ -79,34 +79,6 @@ def test_unknown_option_rejected(lf):
         ctx.close()
 
 
-@pytest.mark.parametrize("prec", [32, 64])
-@pytest.mark.parametrize("p", [2, 3, 5])
-def test_l2_blocked_inner_loop_bit_identical(lf, prec, p):
-    """The inner substeps run block by block (cores with halos of P nodes,
-    draw slabs); with a tiny block budget the mesh splits into many blocks
-    and slabs, and every value must equal the one-launch-per-substep path."""
-    from workload import point_source
-    lev = small_level(n=16, p=p, K=4, box=(0.3, 0.7, 0.3, 0.7))
-    nodes, w = point_source(lev["mesh"], (0.5, 0.52))
-    lev = dict(lev, source={"nodes": nodes, "weights": w, "f0": 5.0, "t0": 0.2, "amp": 1.0})
-    xi = draws(40, 4, seed=p)
-    out = {}
-    for blocked, budget in ((0, 40_000_000), (1, 40_000_000), (1, 20_000), (1, 3_000)):
-        ctx = lf.Context(0)
-        try:
-            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_AUTOTUNE, 0)
-            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_BLOCKED, blocked)
-            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_BLOCK_BUDGET, budget)
-            h = ctx.add_level(lev)
-            out[(blocked, budget)] = ctx.solve(h, xi, precision=prec, state=True)
-        finally:
-            ctx.close()
-    ref = out[(0, 40_000_000)]
-    for k, (Q, U) in out.items():
-        np.testing.assert_array_equal(U, ref[1])
-        np.testing.assert_array_equal(Q, ref[0])
-
-
 def _launches(lf, ctx):
     return lf.lflts_launch_count(ctx.h)
 
