@@ -77,11 +77,19 @@ enum {
   LFLTS_OPT_AUTOTUNE = 2, /* 1 (default): the first solve of a (mesh, S, precision, p) times the
                              candidate launch shapes (draws per thread, CTAs per SM, register cap)
                              and keeps the best */
-  LFLTS_OPT_FUSED_INNER = 5   /* all p-1 inner substeps of a step in one launch, with R's recursion,
+  LFLTS_OPT_FUSED_INNER = 5,  /* all p-1 inner substeps of a step in one launch, with R's recursion,
                                  coupling slots, their edge weights and 1/m for a CTA's draws in
                                  shared memory (only where they fit in 200 KB; same results bit for
                                  bit): 0 never; 1 (default) autotuned, and always where it fits and
                                  |R| <= 2048; 2 always where it fits */
+  LFLTS_OPT_TILED_INNER = 6,  /* all p-1 inner substeps of a step in one launch for a large R: tiles of
+                                 R (a compact core plus p-1 layers of P nodes, recomputed by the
+                                 neighbouring tiles) with each node's state in registers and r_m in
+                                 shared memory; same results bit for bit, uniform batches only:
+                                 0 never; 1 (default) autotuned where |R| > 2048; 2 always (first
+                                 tile shape); 3 always (second tile shape, FP32) */
+  LFLTS_OPT_TILE_CAP = 7      /* 0 (default): tiles as large as the kernel's registers allow; n >= 16:
+                                 at most n computed nodes per tile (more, smaller tiles) */
 };
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -378,8 +386,9 @@ int lflts_profile_read(lflts_ctx* ctx, int kernel_class, int64_t* launches,
 int lflts_launch_count(lflts_ctx* ctx, int64_t* launches);
 
 /* Set an LFLTS_OPT_* option of the context.
- * Errors: LFLTS_ERR_ARG for a NULL context, an unknown option or a fused-inner mode
- * outside {0, 1, 2}. */
+ * Errors: LFLTS_ERR_ARG for a NULL context, an unknown option, a fused-inner mode
+ * outside {0, 1, 2}, a tiled-inner mode outside {0, .., 3} or a tile capacity
+ * in [1, 15] or negative. */
 int lflts_set_option(lflts_ctx* ctx, int option, int64_t value);
 
 /*

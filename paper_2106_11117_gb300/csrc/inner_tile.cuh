@@ -1,0 +1,194 @@
+// All p-1 inner substeps of one outer step (Alg. 2, the loop over m) for a
+// large refined region, tile by tile, with the recursion on chip.
+//
+// The substeps touch only R and couple nodes only through P: r_{m+1} at a
+// node needs r_m at its P neighbours.  A tile is a spatially compact core of
+// R nodes plus p-1 layers of P nodes around it (layer k: the P neighbours of
+// layer k-1 not yet in the tile).  Substep m computes r_{m+1} on the core and
+// layers 1..p-1-m; after the last substep the core's values are exact, since
+// everything they depend on was computed inside the tile.  The outermost
+// layer only supplies r_1 = -c_0 g.  Halo nodes are computed redundantly by
+// every tile that holds them.
+//
+// One CTA takes a (tile, slab of VEC draws) work item.  Thread t owns the
+// tile nodes t, t + NT, ..., t + (IT-1) NT (one node and VEC draws each) and
+// keeps their g, r_m, r_{m-1}, coupling weights and neighbour slots in
+// registers for all substeps; shared memory holds only r_m of the tile for
+// the neighbours' reads (two planes, one per parity of m).  Per step and
+// node the global traffic is g once, the coupling weights once, and u, d in
+// and out on the core, instead of r_m, r_{m-1}, g, the weights and r_{m+1}
+// in every substep.  The arithmetic per node is that of k_inner term by term
+// (same slots in the same order, same roundings, kernels.cuh), so the values
+// are the same bit for bit.
+#pragma once
+#include "kernels.cuh"
+
+namespace lflts {
+
+// Device view of a tile plan (built on the host, mesh_prep.h).
+struct TileDev {
+  const int* ptr;    // [n_tiles + 1] first tile node of every tile
+  const int* len;    // [n_tiles][p]: core size, then core + layers 1..k for k = 1..p-1
+  const int* node;   // mesh node of every tile node
+  const int2* sj;    // [tile node]: four coupling slots as 16-bit pairs (lo, hi) of
+                     //   (local neighbour, -1: a coupling without r (neighbour off P),
+                     //   -2: no slot)
+  const int4* se;    // [tile node]: edge ids of the four slots
+  const int* xp;     // [tile node]: (offset << 4) | count of the slots beyond the fourth
+  const int2* xs;    // those slots: (local neighbour or -1, edge id)
+  int n_tiles;
+  int n_all_max;     // largest tile (shared-memory planes)
+};
+
+__device__ __forceinline__ int slot_of(const int4& v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+// slot q of a node: the signed 16-bit half q % 2 of word q / 2
+__device__ __forceinline__ int slot_of(const int2& v, int q) {
+  const int wd = (q < 2) ? v.x : v.y;
+  return (q & 1) ? (wd >> 16) : int(short(wd & 0xffff));
+}
+
+template <typename Real, int VEC, int IT, int NT>
+__global__ void __launch_bounds__(NT, 1)
+k_inner_tile(TileDev tp, MeshDev<Real> m, int S, const Real* __restrict__ W, const Real* __restrict__ g,
+             const Real* __restrict__ u, Real* __restrict__ u_next, Real* __restrict__ d,
+             const InnerCoef<Real> k, Real kappa) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* const plane0 = reinterpret_cast<Real*>(smem_raw);
+  Real* const plane1 = plane0 + (size_t)tp.n_all_max * VEC;
+  const int p = k.p;
+  const int n_slabs = S / VEC;
+  const int64_t n_work = (int64_t)tp.n_tiles * n_slabs;
+  for (int64_t wk = blockIdx.x; wk < n_work; wk += gridDim.x) {
+    const int t = (int)(wk / n_slabs);
+    const int s0 = (int)(wk % n_slabs) * VEC;  // slabs of one tile are neighbouring work items
+    const int base = tp.ptr[t];
+    const int* len = tp.len + (size_t)t * p;
+    const int n_comp = len[p - 2];  // nodes of the first substep
+    const int n_all = len[p - 1];
+
+    // ---- load: g, r_1 = -c_0 g, coupling weights and slots ---------------
+    Pack<Real, VEC> rc[IT], rp[IT], gi[IT], w[IT][4];
+    int2 sj[IT];
+    Real mi[IT];
+    bool iP[IT];
+    int xp[IT];
+#pragma unroll
+    for (int j = 0; j < IT; ++j) {
+      const int a = threadIdx.x + j * NT;
+      sj[j] = make_int2(int(0xfffefffe), int(0xfffefffe));  // four -2: no slot
+      xp[j] = 0;
+      mi[j] = Real(0);
+      iP[j] = false;
+      if (a < n_comp) {
+        const int node = tp.node[base + a];
+        iP[j] = node < m.n_P;
+        mi[j] = m.minv[node];
+        sj[j] = tp.sj[base + a];
+        xp[j] = tp.xp[base + a];
+        const int4 se = tp.se[base + a];
+        gi[j] = ldp<Real, VEC>(g + (size_t)node * S + s0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (slot_of(sj[j], q) != -2) {
+            w[j][q] = ldp<Real, VEC>(W + (size_t)slot_of(se, q) * S + s0);
+          } else {
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) w[j][q].v[c] = Real(0);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) {
+          rc[j].v[c] = Rn<Real>::mul(k.neg_c0, gi[j].v[c]);
+          rp[j].v[c] = Real(0);
+        }
+        stp<Real, VEC>(plane0 + (size_t)a * VEC, rc[j]);
+      }
+    }
+    for (int a = n_comp + threadIdx.x; a < n_all; a += NT) {  // outermost layer: r_1 only
+      const int node = tp.node[base + a];
+      Pack<Real, VEC> r1 = ldp<Real, VEC>(g + (size_t)node * S + s0);
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) r1.v[c] = Rn<Real>::mul(k.neg_c0, r1.v[c]);
+      stp<Real, VEC>(plane0 + (size_t)a * VEC, r1);
+    }
+    __syncthreads();
+
+    // ---- substeps m = 1 .. p-1 ----------------------------------------------
+    const Real* cur = plane0;
+    Real* nxt = plane1;
+    for (int mm = 1; mm < p; ++mm) {
+      const bool last = (mm == p - 1);
+      const int lm = len[p - 1 - mm];  // core and layers 1..p-1-m
+      const Real opb = k.opb[mm], beta = k.beta[mm], cm = k.cm[mm];
+#pragma unroll
+      for (int j = 0; j < IT; ++j) {
+        const int a = threadIdx.x + j * NT;
+        if (a < lm) {
+          Real vi[VEC], acc[VEC];
+#pragma unroll
+          for (int c = 0; c < VEC; ++c) {
+            vi[c] = iP[j] ? rc[j].v[c] : Real(0);
+            acc[c] = Real(0);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int sl = slot_of(sj[j], q);
+            if (sl != -2) {
+              Pack<Real, VEC> rj;
+              if (sl >= 0) {
+                rj = ldp<Real, VEC>(cur + (size_t)sl * VEC);
+              } else {
+#pragma unroll
+                for (int c = 0; c < VEC; ++c) rj.v[c] = Real(0);
+              }
+#pragma unroll
+              for (int c = 0; c < VEC; ++c) acc[c] = couple(acc[c], w[j][q].v[c], rj.v[c], vi[c]);
+            }
+          }
+          const int nx = xp[j] & 15;
+          for (int e = 0; e < nx; ++e) {  // slots beyond the fourth (a few nodes of graded fans)
+            const int2 o = tp.xs[(xp[j] >> 4) + e];
+            const Pack<Real, VEC> wo = ldp<Real, VEC>(W + (size_t)o.y * S + s0);
+            Pack<Real, VEC> rj;
+            if (o.x >= 0) {
+              rj = ldp<Real, VEC>(cur + (size_t)o.x * VEC);
+            } else {
+#pragma unroll
+              for (int c = 0; c < VEC; ++c) rj.v[c] = Real(0);
+            }
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) acc[c] = couple(acc[c], wo.v[c], rj.v[c], vi[c]);
+          }
+          Pack<Real, VEC> rn;
+#pragma unroll
+          for (int c = 0; c < VEC; ++c)
+            rn.v[c] = inner_next(opb, rc[j].v[c], beta, rp[j].v[c], cm, gi[j].v[c], mi[j], acc[c]);
+          if (!last) {
+            stp<Real, VEC>(nxt + (size_t)a * VEC, rn);
+            rp[j] = rc[j];
+            rc[j] = rn;
+          } else {  // the core: d_{n+1} = d_n + kappa r_p, u_{n+1} = u_n + d_{n+1}
+            const size_t is = (size_t)tp.node[base + a] * S + s0;
+            const Pack<Real, VEC> ui = ldp<Real, VEC>(u + is);
+            Pack<Real, VEC> dn = ldp<Real, VEC>(d + is), un;
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) {
+              dn.v[c] = Rn<Real>::fma(kappa, rn.v[c], dn.v[c]);
+              un.v[c] = Rn<Real>::add(ui.v[c], dn.v[c]);
+            }
+            stp<Real, VEC>(d + is, dn);
+            stp<Real, VEC>(u_next + is, un);
+          }
+        }
+      }
+      __syncthreads();
+      const Real* tmp = cur;
+      cur = nxt;
+      nxt = const_cast<Real*>(tmp);
+    }
+  }
+}
+
+}  // namespace lflts

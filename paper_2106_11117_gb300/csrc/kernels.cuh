@@ -131,6 +131,43 @@ __device__ __forceinline__ double ricker_scaled(const RaggedF& rf, int s) {
 __device__ __forceinline__ float exp2_r(float x) { return exp2f(x); }
 __device__ __forceinline__ double exp2_r(double x) { return exp2(x); }
 
+// Arithmetic of the inner substeps with every rounding written out (no
+// contraction left to the compiler), so that the kernels that run the
+// substeps (one launch per substep, all substeps of a small R, tiles of a
+// large R) produce the same values bit for bit.
+template <typename Real>
+struct Rn;
+template <>
+struct Rn<float> {
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <>
+struct Rn<double> {
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+
+// One coupling term of a(P r_m)_i: acc + W_ij (r_j - v_i), r_j = 0 off P,
+// v_i = r_i on P (0 off P).
+template <typename Real>
+__device__ __forceinline__ Real couple(Real acc, Real w, Real rj, Real vi) {
+  return Rn<Real>::fma(w, Rn<Real>::sub(rj, vi), acc);
+}
+// r_{m+1} = (1 + beta_m) r_m - beta_m r_{m-1} - c_m (g + m_i^-1 acc)
+template <typename Real>
+__device__ __forceinline__ Real inner_next(Real opb, Real rc, Real beta, Real rp, Real cm, Real gi, Real mi,
+                                           Real acc) {
+  const Real a = Rn<Real>::mul(opb, rc);
+  const Real b = Rn<Real>::mul(beta, rp);
+  const Real c = Rn<Real>::mul(cm, Rn<Real>::fma(mi, acc, gi));
+  return Rn<Real>::sub(Rn<Real>::sub(a, b), c);
+}
+
 // Thread -> (node row, sample vector) for blockDim.x = 256 threads.
 struct Lane {
   int sv;   // sample-vector index (samples sv*VEC .. sv*VEC+VEC-1)
@@ -309,12 +346,14 @@ k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
     const Pack<Real, VEC> rc = ldp<Real, VEC>(cur + is);
     const Pack<Real, VEC> gi = ldp<Real, VEC>(g + is);
     Pack<Real, VEC> rj[4], w[4], rp;
+    bool jc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = nb.j[q];
       const bool jP = j >= 0 && j < nP;
       // only P neighbours carry r; a P node also couples to its other neighbours
-      if (jP || (iP && j >= 0)) {
+      jc[q] = jP || (iP && j >= 0);  // a coupling slot (the others add nothing)
+      if (jc[q]) {
         w[q] = ldp<Real, VEC>(W + (size_t)nb.e[q] * S + s0);
       } else {
 #pragma unroll
@@ -337,13 +376,14 @@ k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
     Real vi[VEC], acc[VEC];
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
-      vi[k] = iP ? s_cur * rc.v[k] : Real(0);
+      vi[k] = iP ? Rn<Real>::mul(s_cur, rc.v[k]) : Real(0);
       acc[k] = Real(0);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
+      if (jc[q])
 #pragma unroll
-      for (int k = 0; k < VEC; ++k) acc[k] = fma(w[q].v[k], s_cur * rj[q].v[k] - vi[k], acc[k]);
+        for (int k = 0; k < VEC; ++k) acc[k] = couple(acc[k], w[q].v[k], Rn<Real>::mul(s_cur, rj[q].v[k]), vi[k]);
     for (int t = t0; t < t1; ++t) {  // neighbours beyond the fourth (rare)
       const int2 o = m.adj[t];
       const bool jP = o.x < nP;
@@ -352,23 +392,24 @@ k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
       if (jP) {
         const Pack<Real, VEC> ro = ldp<Real, VEC>(cur + (size_t)o.x * S + s0);
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] = fma(wo.v[k], s_cur * ro.v[k] - vi[k], acc[k]);
+        for (int k = 0; k < VEC; ++k) acc[k] = couple(acc[k], wo.v[k], Rn<Real>::mul(s_cur, ro.v[k]), vi[k]);
       } else {
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] = fma(wo.v[k], -vi[k], acc[k]);
+        for (int k = 0; k < VEC; ++k) acc[k] = couple(acc[k], wo.v[k], Rn<Real>::mul(s_cur, Real(0)), vi[k]);
       }
     }
     Pack<Real, VEC> rn;
 #pragma unroll
     for (int k = 0; k < VEC; ++k)
-      rn.v[k] = one_plus_beta * (s_cur * rc.v[k]) - beta * (s_prev * rp.v[k]) - cm * (gi.v[k] + mi * acc[k]);
+      rn.v[k] = inner_next(one_plus_beta, Rn<Real>::mul(s_cur, rc.v[k]), beta, Rn<Real>::mul(s_prev, rp.v[k]), cm,
+                           gi.v[k], mi, acc[k]);
     if (LAST) {
       const Pack<Real, VEC> ui = ldp<Real, VEC>(u + is);
       Pack<Real, VEC> dn = ldp<Real, VEC>(d + is), un;
 #pragma unroll
       for (int k = 0; k < VEC; ++k) {
-        dn.v[k] = dn.v[k] + kappa * rn.v[k];
-        un.v[k] = ui.v[k] + dn.v[k];
+        dn.v[k] = Rn<Real>::fma(kappa, rn.v[k], dn.v[k]);
+        un.v[k] = Rn<Real>::add(ui.v[k], dn.v[k]);
       }
       if constexpr (RAG) {
         stp_lim<Real, VEC>(d + is, dn, nvalid);
@@ -467,7 +508,7 @@ k_inner_fused(MeshDev<Real> m, int S, int SBf, const Real* __restrict__ W, const
         Real vi[VEC], acc[VEC];
 #pragma unroll
         for (int kk = 0; kk < VEC; ++kk) {
-          vi[kk] = iP ? s_cur * rc.v[kk] : Real(0);
+          vi[kk] = iP ? Rn<Real>::mul(s_cur, rc.v[kk]) : Real(0);
           acc[kk] = Real(0);
         }
         const int t1 = sptr[i + 1];
@@ -482,21 +523,22 @@ k_inner_fused(MeshDev<Real> m, int S, int SBf, const Real* __restrict__ W, const
             for (int kk = 0; kk < VEC; ++kk) rj.v[kk] = Real(0);
           }
 #pragma unroll
-          for (int kk = 0; kk < VEC; ++kk) acc[kk] = fma(w.v[kk], s_cur * rj.v[kk] - vi[kk], acc[kk]);
+          for (int kk = 0; kk < VEC; ++kk) acc[kk] = couple(acc[kk], w.v[kk], Rn<Real>::mul(s_cur, rj.v[kk]), vi[kk]);
         }
         const Real mi = sminv[i];
         Pack<Real, VEC> rn;
 #pragma unroll
         for (int kk = 0; kk < VEC; ++kk)
-          rn.v[kk] = one_plus_beta * (s_cur * rc.v[kk]) - beta * (s_prev * rp.v[kk]) - cm * (gi.v[kk] + mi * acc[kk]);
+          rn.v[kk] = inner_next(one_plus_beta, Rn<Real>::mul(s_cur, rc.v[kk]), beta, Rn<Real>::mul(s_prev, rp.v[kk]),
+                                cm, gi.v[kk], mi, acc[kk]);
         if (last) {
           const size_t is = (size_t)i * S + s0;
           const Pack<Real, VEC> ui = ldp<Real, VEC>(u + is);
           Pack<Real, VEC> dn = ldp<Real, VEC>(d + is), un;
 #pragma unroll
           for (int kk = 0; kk < VEC; ++kk) {
-            dn.v[kk] = dn.v[kk] + kappa * rn.v[kk];
-            un.v[kk] = ui.v[kk] + dn.v[kk];
+            dn.v[kk] = Rn<Real>::fma(kappa, rn.v[kk], dn.v[kk]);
+            un.v[kk] = Rn<Real>::add(ui.v[kk], dn.v[kk]);
           }
           if constexpr (RAG) {
             stp_lim<Real, VEC>(d + is, dn, nvalid);

@@ -23,6 +23,7 @@
 
 #include "../../include/lflts.h"
 #include "adjoint.cuh"
+#include "inner_tile.cuh"
 #include "kernels.cuh"
 #include "mesh_prep.h"
 
@@ -59,6 +60,12 @@ struct MeshGPU {
   int64_t n_rslots = -1;
   // autotuned (vec, shape code) per (S, precision, p)
   std::map<std::tuple<int64_t, int, int>, std::pair<int, int>> tuned;
+  // tile plans of the on-chip inner substeps per (p, tile capacity), uploaded
+  struct DevTiles {
+    TileDev dev{};
+    bool ok = false;
+  };
+  std::map<std::pair<int, int64_t>, DevTiles> tiles;
 };
 
 struct Field {
@@ -154,6 +161,8 @@ struct lflts_ctx {
   bool graphs = true;
   bool autotune = true;
   int fused_mode = 1;            // fused inner kernel: 0 never, 1 autotuned, 2 always where it fits
+  int tile_mode = 1;             // tiled inner kernel: 0 never, 1 autotuned, 2/3 always (first/second shape)
+  int64_t tile_cap = 0;          // > 0: at most this many computed nodes per tile
   std::vector<void*> owned;  // device allocations of meshes, fields, QoIs
   std::unique_ptr<PairRun> run;  // lflts_run_pairs_slice: the run in progress, if any
   ~lflts_ctx();
@@ -380,6 +389,53 @@ inline void fused_plan(const lflts_ctx* c, int n_R, int64_t n_slots, int64_t S, 
   if (need <= kFusedSmemMax) smem = need;
 }
 
+// Launch shapes of the tiled inner kernel: draws per node (VEC), nodes per
+// thread (IT) and threads (NT); a tile holds at most IT * NT computed nodes.
+// All keep their per-node state in registers without spills (ptxas -v).
+struct TileShape {
+  int vec, it, nt;
+};
+template <typename Real>
+int tile_shapes() {
+  return sizeof(Real) == 4 ? 2 : 1;
+}
+template <typename Real>
+TileShape tile_shape(int var) {
+  if (sizeof(Real) == 8) return {2, 3, 384};
+  return var == 0 ? TileShape{4, 3, 384} : TileShape{2, 6, 384};
+}
+template <typename Real>
+int64_t tile_cap(const lflts_ctx* c, int var) {
+  const TileShape ts = tile_shape<Real>(var);
+  const int64_t cap = int64_t(ts.it) * ts.nt;
+  return c->tile_cap > 0 ? std::min<int64_t>(c->tile_cap, cap) : cap;
+}
+template <typename Real>
+size_t tile_smem(const TileDev& td, int var) {
+  return size_t(2) * size_t(td.n_all_max) * size_t(tile_shape<Real>(var).vec) * sizeof(Real);
+}
+constexpr size_t kTileSmemMax = 220 * 1024;
+
+template <typename Real>
+cudaError_t tile_attr(int var, int smem) {
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (sizeof(Real) == 8) return cudaFuncSetAttribute(k_inner_tile<Real, 2, 3, 384>, attr, smem);
+  if (var == 0) return cudaFuncSetAttribute(k_inner_tile<Real, 4, 3, 384>, attr, smem);
+  return cudaFuncSetAttribute(k_inner_tile<Real, 2, 6, 384>, attr, smem);
+}
+
+template <typename Real>
+void tile_launch(int var, int grid, size_t smem, cudaStream_t st, const TileDev& td, const MeshDev<Real>& md,
+                 int S, const Real* W, const Real* g, const Real* u, Real* un, Real* d, const InnerCoef<Real>& k,
+                 Real kappa) {
+  if (sizeof(Real) == 8)
+    k_inner_tile<Real, 2, 3, 384><<<grid, 384, smem, st>>>(td, md, S, W, g, u, un, d, k, kappa);
+  else if (var == 0)
+    k_inner_tile<Real, 4, 3, 384><<<grid, 384, smem, st>>>(td, md, S, W, g, u, un, d, k, kappa);
+  else
+    k_inner_tile<Real, 2, 6, 384><<<grid, 384, smem, st>>>(td, md, S, W, g, u, un, d, k, kappa);
+}
+
 // One step of Alg. 2 for one batch (see kernels.cuh for the u-form): the
 // coarse launch over the free nodes, then p-1 inner launches over R (or one
 // fused launch for a small R).
@@ -402,6 +458,10 @@ struct Stepper {
   int fSB = 1;
   size_t fsmem = 0;
   int fgrid = 1;
+  int tvar = -1;       // tiled inner kernel shape (-1: not tiled)
+  TileDev tdev{};
+  size_t tsmem = 0;
+  int tgrid = 1;
   InnerCoef<Real> coef{};
   const Real* fw = nullptr;  // M^-1 F or null
   double f0 = 0, t0 = 0, famp = 0, dt = 0;
@@ -441,11 +501,24 @@ struct Stepper {
     gi = geometry_vec(c, std::max(n_R, 1), S, VEC, cta_per_sm);
     Srb = double(S) * sizeof(Real);
     coarse_bytes = 3.0 * Srb * double(h.n_free);
-    if (shape >= 2000 && n_R > 0 && p > 1 && p <= 64) {
-      fused_plan(c, n_R, mg.n_rslots, S, VEC, sizeof(Real), fSB, fsmem);
-      fused = fsmem > 0;
-      const int64_t SL = int64_t(fSB) * VEC;
-      fgrid = static_cast<int>((S + SL - 1) / SL);
+    const int kind = shape / 1000;  // 0 per substep, 2 fused, 3.. tiled (shape kind - 3)
+    if (kind >= 3 && n_R > 0 && p > 1 && p <= 64 && S % tile_shape<Real>(kind - 3).vec == 0) {
+      auto it = mg.tiles.find(std::make_pair(p, tile_cap<Real>(c, kind - 3)));
+      if (it != mg.tiles.end() && it->second.ok) {
+        tvar = kind - 3;
+        tdev = it->second.dev;
+        tsmem = tile_smem<Real>(tdev, tvar);
+        const int64_t work = int64_t(tdev.n_tiles) * (S / tile_shape<Real>(tvar).vec);
+        tgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(work, c->sms)));
+      }
+    }
+    if (kind >= 2 && n_R > 0 && p > 1 && p <= 64) {
+      if (kind == 2) {
+        fused_plan(c, n_R, mg.n_rslots, S, VEC, sizeof(Real), fSB, fsmem);
+        fused = fsmem > 0;
+        const int64_t SL = int64_t(fSB) * VEC;
+        fgrid = static_cast<int>((S + SL - 1) / SL);
+      }
       coef.p = p;
       coef.neg_c0 = (Real)(-c0);
       for (int m = 1; m < p; ++m) {
@@ -509,6 +582,14 @@ struct Stepper {
 #undef LF_COARSE
       LF_CUDA(c, cudaGetLastError());
       pr.end(LFLTS_KERNEL_COARSE, coarse_bytes);
+    }
+    if (n_R > 0 && tvar >= 0 && !dts) {
+      Prof pr(c, st);
+      tile_launch<Real>(tvar, tgrid, tsmem, st, tdev, md, (int)S, W, g, uc, un, d, coef, kappa);
+      LF_CUDA(c, cudaGetLastError());
+      // all substeps on chip: the outer-step bytes of R remain
+      pr.end(LFLTS_KERNEL_INNER, 3.0 * n_R * Srb);
+      return 0;
     }
     if (n_R > 0 && fused) {
       Prof pr(c, st);
@@ -630,6 +711,54 @@ bool fused_ok(lflts_ctx* c, MeshGPU& mg, int n_R, int64_t S, int vec, int p) {
   return e == cudaSuccess;
 }
 
+// Whether the tiled inner kernel of shape `var` can run this batch: builds
+// and uploads the mesh's tile plan for (p, capacity) once and raises the
+// kernel's dynamic shared-memory limit (outside any graph capture).
+template <typename Real>
+bool tile_ok(lflts_ctx* c, MeshGPU& mg, int n_R, int64_t S, int p, int var) {
+  if (n_R < 1 || p < 2 || p > 64 || var < 0 || var >= tile_shapes<Real>()) return false;
+  if (S % tile_shape<Real>(var).vec != 0) return false;
+  const auto key = std::make_pair(p, tile_cap<Real>(c, var));
+  auto it = mg.tiles.find(key);
+  if (it == mg.tiles.end()) {
+    MeshGPU::DevTiles dt;
+    TilePlan tp;
+    if (build_tile_plan(mg.h, p, key.second, tp)) {
+      int* d_ptr = nullptr;
+      int* d_len = nullptr;
+      int* d_node = nullptr;
+      int* d_sj = nullptr;
+      int* d_se = nullptr;
+      int* d_xp = nullptr;
+      int* d_xs = nullptr;
+      const bool up = !upload(c, &d_ptr, tp.ptr.data(), tp.ptr.size()) &&
+                      !upload(c, &d_len, tp.len.data(), tp.len.size()) &&
+                      !upload(c, &d_node, tp.node.data(), tp.node.size()) &&
+                      !upload(c, &d_sj, tp.sj.data(), tp.sj.size()) &&
+                      !upload(c, &d_se, tp.se.data(), tp.se.size()) &&
+                      !upload(c, &d_xp, tp.xp.data(), tp.xp.size()) &&
+                      !upload(c, &d_xs, tp.xs.data(), tp.xs.size());
+      if (up) {
+        dt.dev.ptr = d_ptr;
+        dt.dev.len = d_len;
+        dt.dev.node = d_node;
+        dt.dev.sj = reinterpret_cast<const int2*>(d_sj);
+        dt.dev.se = reinterpret_cast<const int4*>(d_se);
+        dt.dev.xp = d_xp;
+        dt.dev.xs = reinterpret_cast<const int2*>(d_xs);
+        dt.dev.n_tiles = static_cast<int>(tp.ptr.size()) - 1;
+        dt.dev.n_all_max = static_cast<int>(tp.n_all_max);
+        dt.ok = true;
+      }
+    }
+    it = mg.tiles.emplace(key, dt).first;
+  }
+  if (!it->second.ok) return false;
+  const size_t smem = tile_smem<Real>(it->second.dev, var);
+  if (smem > kTileSmemMax) return false;
+  return tile_attr<Real>(var, static_cast<int>(kTileSmemMax)) == cudaSuccess;
+}
+
 // Draw segments of a ragged batch: draws [off, off + cnt) take n_steps steps
 // of dt.  Segments are sorted by n_steps, descending, so that the draws still
 // stepping always form a prefix of the batch.  A uniform batch is one segment.
@@ -749,6 +878,10 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
     if (S % v == 0) vecs.push_back(v);
   vec = vecs.front();
   cps = 16;
+  if (c->tile_mode >= 2 && !dts && tile_ok<Real>(c, mg, n_R, S, ds.p, c->tile_mode - 2)) {
+    cps = 3016 + 1000 * (c->tile_mode - 2);
+    return 0;
+  }
   if (c->fused_mode == 2 && fused_ok<Real>(c, mg, n_R, S, vec, ds.p)) {
     cps = 2016;
     return 0;
@@ -782,6 +915,12 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
       if (n_R <= 2048) shapes.clear();
       for (int k : {8, 16, 32, 108, 116, 132}) shapes.push_back(2000 + k);
     }
+    // the tiled inner kernel (all substeps on chip) for a large R; its own
+    // draws per node do not depend on v, so it is timed with the first v only
+    if (c->tile_mode == 1 && !dts && n_R > 2048 && v == vecs.front())
+      for (int var = 0; var < tile_shapes<Real>(); ++var)
+        if (tile_ok<Real>(c, mg, n_R, S, ds.p, var))
+          for (int k : {8, 16, 32, 108, 116, 132}) shapes.push_back(3000 + 1000 * var + k);
     for (int k : shapes) {
       Real* uc = nullptr;
       int rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, v, k, 1, dts);  // warm
@@ -2036,6 +2175,17 @@ int lflts_set_option(lflts_ctx* c, int option, int64_t value) {
       if (value < 0 || value > 2) return fail(c, LFLTS_ERR_ARG, "set_option: fused inner mode must be 0, 1 or 2");
       c->fused_mode = static_cast<int>(value);
       for (auto& m : c->meshes) m->tuned.clear();  // re-tune with the new candidate set
+      return LFLTS_OK;
+    case LFLTS_OPT_TILED_INNER:
+      if (value < 0 || value > 3) return fail(c, LFLTS_ERR_ARG, "set_option: tiled inner mode must be 0..3");
+      c->tile_mode = static_cast<int>(value);
+      for (auto& m : c->meshes) m->tuned.clear();
+      return LFLTS_OK;
+    case LFLTS_OPT_TILE_CAP:
+      if (value < 0 || (value > 0 && value < 16))
+        return fail(c, LFLTS_ERR_ARG, "set_option: tile capacity must be 0 or at least 16");
+      c->tile_cap = value;
+      for (auto& m : c->meshes) m->tuned.clear();
       return LFLTS_OK;
     default: return fail(c, LFLTS_ERR_ARG, "set_option: unknown option");
   }

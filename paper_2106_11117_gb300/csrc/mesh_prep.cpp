@@ -350,14 +350,11 @@ void build_r_slots(const HostMesh& m, std::vector<int32_t>& ptr, std::vector<int
   }
 }
 
-void build_inner_blocks(const HostMesh& m, int p, int64_t core, InnerBlocks& out) {
-  const int64_t nR = m.n_R, nP = m.n_P;
-  out.nodes.clear();
-  out.start.assign(1, 0);
-  out.layer_end.clear();
-  if (nR == 0 || p < 2) return;
-  core = std::max<int64_t>(core, 1);
-  // Morton order of R by coordinates
+namespace {
+
+// R's nodes in Morton order of their coordinates.
+std::vector<int32_t> morton_order_R(const HostMesh& m) {
+  const int64_t nR = m.n_R;
   double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
   for (int64_t i = 0; i < nR; ++i) {
     x0 = std::min(x0, m.xy[2 * i]);
@@ -373,36 +370,115 @@ void build_inner_blocks(const HostMesh& m, int p, int64_t core, InnerBlocks& out
     key[i] = {morton_spread16(qx) | (morton_spread16(qy) << 1), static_cast<int32_t>(i)};
   }
   std::sort(key.begin(), key.end());
-  const int64_t n_blocks = (nR + core - 1) / core;
-  std::vector<int64_t> stamp(nR, -1);
-  std::vector<int32_t> frontier, next;
-  for (int64_t b = 0; b < n_blocks; ++b) {
-    const int64_t a0 = b * nR / n_blocks, a1 = (b + 1) * nR / n_blocks;
-    const size_t base = out.nodes.size();
-    frontier.clear();
-    for (int64_t a = a0; a < a1; ++a) {
-      const int32_t i = key[a].second;
-      stamp[i] = b;
-      out.nodes.push_back(i);
-      frontier.push_back(i);
+  std::vector<int32_t> out(nR);
+  for (int64_t a = 0; a < nR; ++a) out[a] = key[a].second;
+  return out;
+}
+
+// Nodes of one tile: the core order[a0, a1), then `layers` layers of P
+// nodes (BFS through P neighbours); lens receives core + layers 1..k for
+// k = 0..layers.  stamp/mark: per-node scratch, stamp[i] == mark means in
+// the tile.
+void tile_nodes(const HostMesh& m, const std::vector<int32_t>& order, int64_t a0, int64_t a1, int layers,
+                std::vector<int64_t>& stamp, int64_t mark, std::vector<int32_t>& nodes,
+                std::vector<int32_t>& lens) {
+  const int64_t nP = m.n_P;
+  nodes.clear();
+  lens.clear();
+  for (int64_t a = a0; a < a1; ++a) {
+    stamp[order[a]] = mark;
+    nodes.push_back(order[a]);
+  }
+  lens.push_back(static_cast<int32_t>(nodes.size()));
+  size_t f0 = 0;
+  for (int k = 1; k <= layers; ++k) {
+    const size_t f1 = nodes.size();
+    for (size_t f = f0; f < f1; ++f) {
+      const int32_t i = nodes[f];
+      for (int32_t t = m.adj_ptr[i]; t < m.adj_ptr[i + 1]; ++t) {
+        const int32_t j = m.adj_j[t];
+        if (j < nP && stamp[j] != mark) {
+          stamp[j] = mark;
+          nodes.push_back(j);
+        }
+      }
     }
-    out.layer_end.push_back(static_cast<int32_t>(out.nodes.size() - base));
-    for (int k = 1; k <= p - 2; ++k) {  // halo layer k: P neighbours of layer k-1
-      next.clear();
-      for (int32_t i : frontier)
-        for (int32_t t = m.adj_ptr[i]; t < m.adj_ptr[i + 1]; ++t) {
-          const int32_t j = m.adj_j[t];
-          if (j < nP && stamp[j] != b) {
-            stamp[j] = b;
-            next.push_back(j);
-            out.nodes.push_back(j);
+    f0 = f1;
+    lens.push_back(static_cast<int32_t>(nodes.size()));
+  }
+}
+
+}  // namespace
+
+bool build_tile_plan(const HostMesh& m, int p, int64_t cap, TilePlan& out) {
+  out = TilePlan();
+  const int64_t nR = m.n_R;
+  if (nR == 0 || p < 2 || cap < 16) return false;
+  std::vector<int32_t> rptr, rsj, rse;
+  build_r_slots(m, rptr, rsj, rse);
+  const std::vector<int32_t> order = morton_order_R(m);
+  std::vector<int64_t> stamp(std::max<int64_t>(m.n_free, nR), -1);
+  std::vector<int32_t> nodes, lens;
+  int64_t mark = 0;
+  // core size: shrink until the computed part (core + layers 1..p-2) of
+  // every tile fits `cap`
+  int64_t core = std::min<int64_t>(nR, std::max<int64_t>(1, cap / 2));
+  for (int attempt = 0;; ++attempt) {
+    const int64_t n_tiles = (nR + core - 1) / core;
+    int64_t worst = 0;
+    for (int64_t t = 0; t < n_tiles; ++t) {
+      tile_nodes(m, order, t * nR / n_tiles, (t + 1) * nR / n_tiles, p - 1, stamp, mark++, nodes, lens);
+      worst = std::max<int64_t>(worst, lens[p - 2]);
+      if (lens[p - 1] > 32767) return false;
+    }
+    if (worst <= cap) break;
+    if (core == 1 || attempt > 60) return false;
+    core = std::max<int64_t>(1, std::min<int64_t>(core - 1, static_cast<int64_t>(core * 0.95 * double(cap) / double(worst))));
+  }
+  const int64_t n_tiles = (nR + core - 1) / core;
+  out.p = p;
+  out.cap = static_cast<int>(cap);
+  out.ptr.assign(1, 0);
+  std::vector<int32_t> local(std::max<int64_t>(m.n_free, nR), -1);
+  for (int64_t t = 0; t < n_tiles; ++t) {
+    tile_nodes(m, order, t * nR / n_tiles, (t + 1) * nR / n_tiles, p - 1, stamp, mark, nodes, lens);
+    for (size_t a = 0; a < nodes.size(); ++a) local[nodes[a]] = static_cast<int32_t>(a);
+    const int32_t n_comp = lens[p - 2];
+    for (size_t a = 0; a < nodes.size(); ++a) {
+      const int32_t i = nodes[a];
+      out.node.push_back(i);
+      int32_t q4[4] = {-2, -2, -2, -2}, e4[4] = {0, 0, 0, 0};
+      int32_t xoff = static_cast<int32_t>(out.xs.size() / 2), xcnt = 0;
+      if (static_cast<int32_t>(a) < n_comp) {
+        for (int32_t s = rptr[i]; s < rptr[i + 1]; ++s) {
+          int32_t lj = -1;
+          if (rsj[s] >= 0) {
+            if (stamp[rsj[s]] != mark) return false;  // cannot happen: the layers close the tile
+            lj = local[rsj[s]];
+          }
+          const int32_t q = s - rptr[i];
+          if (q < 4) {
+            q4[q] = lj;
+            e4[q] = rse[s];
+          } else {
+            out.xs.push_back(lj);
+            out.xs.push_back(rse[s]);
+            ++xcnt;
           }
         }
-      frontier.swap(next);
-      out.layer_end.push_back(static_cast<int32_t>(out.nodes.size() - base));
+        if (xcnt > 15) return false;
+      }
+      out.sj.push_back(static_cast<int32_t>((uint32_t(uint16_t(q4[0]))) | (uint32_t(uint16_t(q4[1])) << 16)));
+      out.sj.push_back(static_cast<int32_t>((uint32_t(uint16_t(q4[2]))) | (uint32_t(uint16_t(q4[3])) << 16)));
+      for (int q = 0; q < 4; ++q) out.se.push_back(e4[q]);
+      out.xp.push_back(xcnt ? ((xoff << 4) | xcnt) : 0);
     }
-    out.start.push_back(static_cast<int64_t>(out.nodes.size()));
+    for (int k = 0; k < p; ++k) out.len.push_back(lens[k]);
+    out.n_all_max = std::max<int64_t>(out.n_all_max, static_cast<int64_t>(nodes.size()));
+    out.ptr.push_back(static_cast<int32_t>(out.node.size()));
+    ++mark;
   }
+  return true;
 }
 
 }  // namespace lflts

@@ -51,23 +51,6 @@ struct HostMesh {
   std::vector<double> xy;                  // [n_nodes][2] coordinates, internal order
 };
 
-// Blocks of the inner substeps for L2 residency.  Block b computes the p-1
-// substeps of Alg. 2 on its core nodes for a slab of draws; substep m
-// (1 <= m <= p-1) runs on the prefix of the block's node list made of the
-// core and the first p-1-m halo layers, where halo layer k holds the P nodes
-// at k P-neighbour hops from the core.  After p-1 substeps the core values
-// are exact: every value they depend on was computed inside the block.
-struct InnerBlocks {
-  int64_t slab = 0;                    // draws per block
-  std::vector<int32_t> nodes;          // concatenated node lists (internal ids)
-  std::vector<int64_t> start;          // [n_blocks + 1] offsets into nodes
-  std::vector<int32_t> layer_end;      // [n_blocks][p-1]: prefix length for halo depth 0..p-2
-};
-
-// Partition R into spatially compact blocks of about `core` nodes (Morton
-// order of the node coordinates) and attach p-2 halo layers.
-void build_inner_blocks(const HostMesh& m, int p, int64_t core, InnerBlocks& out);
-
 // Coupling slots of the inner substeps on R, in the order the per-substep
 // kernel visits them (the four table entries, then the rest of the
 // adjacency list), without the slots that add nothing: node i < n_R keeps
@@ -76,6 +59,29 @@ void build_inner_blocks(const HostMesh& m, int p, int64_t core, InnerBlocks& out
 // n_R + 1 offsets.
 void build_r_slots(const HostMesh& m, std::vector<int32_t>& ptr, std::vector<int32_t>& slot_j,
                    std::vector<int32_t>& slot_e);
+
+// Tiles of the on-chip inner substeps (k_inner_tile).  Tile t holds the
+// nodes node[ptr[t] .. ptr[t+1]): a core of R nodes (a Morton-contiguous
+// range of R), then p-1 layers of P nodes, layer k being the P neighbours of
+// layer k-1 that are not in the tile yet.  len[t*p + k] = core + layers 1..k
+// (k = 0..p-1).  Substep m computes the prefix len[p-1-m]; the first
+// len[p-2] nodes (at most `cap`) are the computed ones.  For every tile node
+// the first four coupling slots of the per-substep kernel's visiting order
+// (build_r_slots) as (local neighbour index, -1 for a neighbour off P, -2
+// for no slot) in 16-bit halves of sj[2 a], sj[2 a + 1], their edge ids in
+// se[4 a + q], and the slots beyond the fourth in xs as (local or -1, edge)
+// pairs from offset xp[a] >> 4, count xp[a] & 15.
+struct TilePlan {
+  int p = 0, cap = 0;
+  int64_t n_all_max = 0;               // largest tile
+  std::vector<int32_t> ptr, len, node;
+  std::vector<int32_t> sj, se, xp, xs;
+};
+
+// Build the plan for tiles of at most `cap` computed nodes; false (and an
+// empty plan) when R is empty, p < 2, a tile would exceed 32767 nodes or a
+// node has more than 15 slots beyond the fourth.
+bool build_tile_plan(const HostMesh& m, int p, int64_t cap, TilePlan& out);
 
 // Nodal interpolation between two triangulations of one domain: for every
 // point xy_f[k] the vertices vert[3k..3k+2] of a triangle of (xy_c, tri_c)

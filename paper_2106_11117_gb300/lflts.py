@@ -43,6 +43,8 @@ EXPORTED = [
 LFLTS_OPT_GRAPHS = 1
 LFLTS_OPT_AUTOTUNE = 2
 LFLTS_OPT_FUSED_INNER = 5
+LFLTS_OPT_TILED_INNER = 6
+LFLTS_OPT_TILE_CAP = 7
 
 
 class LibraryNotBuilt(RuntimeError):
