@@ -117,17 +117,22 @@ class ShardedLevelPairs:
 
     Draws are independent (the MLMC sample is an independent sample,
     Sec. 2.2), so rank r evaluates rows [n r / world, n (r+1) / world) of each
-    request with its own evaluator.  The only exchange is the level sums:
-    every rank all-gathers the per-rank 4-vectors and adds them with
-    compensated summation in rank order, so all ranks take identical Alg. 1
-    decisions.  ``gather(vec) -> list of vecs`` is the collective (e.g.
-    torch.distributed.all_gather_object); dQ stays local."""
+    request with its own evaluator.  The only exchange is the level sums, in
+    one FP64 all-reduce: every rank writes its (sum, compensation) pairs of
+    the 4 sums of every requested level into its own slot of a
+    [world, levels, 4, 2] array that is zero elsewhere, the all-reduce adds
+    the arrays (adding zeros is exact, so every rank receives every pair
+    unchanged, whatever the reduction order), and each level sum is then the
+    compensated sum (math.fsum) of all pairs in rank order -- the same value
+    on every rank, so all ranks take identical Alg. 1 decisions.
+    ``allreduce(array) -> array`` is the collective (sum; e.g. a wrapper of
+    torch.distributed.all_reduce, see ``torch_allreduce``); dQ stays local."""
 
-    def __init__(self, evaluator, rank, world, gather):
+    def __init__(self, evaluator, rank, world, allreduce):
         self.ev = evaluator
         self.rank = rank
         self.world = world
-        self.gather = gather
+        self.allreduce = allreduce
         self.calls = 0
 
     def run(self, requests):
@@ -139,13 +144,38 @@ class ShardedLevelPairs:
         nonempty = {l: x for l, x in local.items() if x.shape[0] > 0}
         res = self.ev.run(nonempty) if nonempty else {}
         self.calls += 1
-        mine = {l: (list(res[l][1]) if l in res else [0.0, 0.0, 0.0, 0.0]) for l in requests}
-        allv = self.gather(mine)
+        levels = sorted(requests)
+        buf = np.zeros((self.world, len(levels), 4, 2))
+        for k, l in enumerate(levels):
+            if l in res:
+                for j, v in enumerate(res[l][1]):
+                    buf[self.rank, k, j] = pairs(v)
+        tot = np.asarray(self.allreduce(buf), dtype=np.float64).reshape(buf.shape)
         out = {}
-        for l in requests:
-            sums = [_csum(v[l][k] for v in allv) for k in range(4)]
+        for k, l in enumerate(levels):
+            sums = [_csum(x for r in range(self.world) for x in tot[r, k, j]) for j in range(4)]
             out[l] = (res[l][0] if l in res else np.zeros(0), sums)
         return out
+
+
+def pairs(v):
+    """(sum, compensation) of a value: a float, or a pair already."""
+    if isinstance(v, (tuple, list, np.ndarray)) and len(v) == 2:
+        return float(v[0]), float(v[1])
+    return float(v), 0.0
+
+
+def torch_allreduce(group=None, device="cpu"):
+    """Sum all-reduce of a numpy FP64 array over torch.distributed (gloo on
+    CPU tensors, NCCL on CUDA tensors)."""
+    import torch
+    import torch.distributed as dist
+
+    def red(a):
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(device)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        return t.cpu().numpy()
+    return red
 
 
 # ------------------------------------------------------------ Alg. 1

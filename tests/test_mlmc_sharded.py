@@ -1,6 +1,7 @@
 """Sharded MLMC on CPU ranks (gloo, world size 2): every rank evaluates its
-block of each level's draws and the ranks combine only the FP64 level sums;
-the result equals the single-process Alg. 1."""
+block of each level's draws and the ranks combine only the FP64 level sums,
+as (sum, compensation) pairs in one all-reduce; the result equals the
+single-process Alg. 1."""
 import math
 import os
 import socket
@@ -26,12 +27,7 @@ def _worker(rank, world, port, out_q):
     from paper_2106_11117_gb300 import mlmc
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
     try:
-        def gather(obj):
-            lst = [None] * world
-            dist.all_gather_object(lst, obj)
-            return lst
-
-        ev = mlmc.ShardedLevelPairs(SyntheticPairs(), rank, world, gather)
+        ev = mlmc.ShardedLevelPairs(SyntheticPairs(), rank, world, mlmc.torch_allreduce())
         r = mlmc.alg1(ev, _draw, 2e-3, cost=lambda l: 4.0**l, N_init=lambda l: 33, alpha=2.0)
         out_q.put((rank, r.estimate, r.L, r.N, r.mse))
     finally:
@@ -74,15 +70,40 @@ def test_shard_blocks_cover_all_draws():
 
     xi = np.arange(21, dtype=float).reshape(7, 3)
     recs = [Rec() for _ in range(3)]
-    parts = {}
-
-    def gather_for(r):
-        def g(obj):
-            parts[r] = obj
-            return [parts.get(k, obj) for k in range(3)]
-        return g
-
     for r in range(3):
-        mlmc.ShardedLevelPairs(recs[r], r, 3, gather_for(r)).run({0: xi})
+        mlmc.ShardedLevelPairs(recs[r], r, 3, lambda a: a).run({0: xi})
     rows = np.concatenate([recs[r].seen[0][0] for r in range(3)])
     np.testing.assert_array_equal(rows, xi)
+
+
+def test_pairs_combine_exactly_in_rank_order():
+    """The all-reduce adds arrays that are zero outside each rank's slot, so
+    every pair arrives unchanged; the level sum is the correctly rounded sum
+    of all pairs (math.fsum), which a plain sum of the rank values misses."""
+    from paper_2106_11117_gb300 import mlmc
+
+    vals = [1e16, 1.0, -1e16, 1.0]     # plain left-to-right sum: 1.0 (1e16 + 1 rounds)
+
+    class One:
+        def __init__(self, v):
+            self.v = v
+
+        def run(self, req):
+            return {l: (np.zeros(1), [self.v, 0.0, 0.0, 0.0]) for l in req}
+
+    bufs = {}
+
+    def red_for(r):
+        def red(a):
+            bufs[r] = a
+            return sum(bufs.get(k, np.zeros_like(a)) for k in range(4))
+        return red
+
+    outs = []
+    for r in range(4):   # the last rank sees every slot filled
+        outs.append(mlmc.ShardedLevelPairs(One(vals[r]), r, 4, red_for(r)).run({0: np.zeros((4, 1))}))
+    assert outs[-1][0][1][0] == 2.0
+    naive = 0.0
+    for v in vals:
+        naive += v
+    assert math.fsum(vals) == 2.0 and naive == 1.0
