@@ -305,6 +305,40 @@ int lflts_run_pairs_slice(lflts_ctx* ctx, const lflts_pair_job* jobs, int n_jobs
                           int mem, int slice, int n_slices, void* stream);
 
 /*
+ * Register the nodal interpolation from mesh_c to mesh_f (both registered,
+ * same domain), as lflts_interp_weights returns it: for every node k of
+ * mesh_f (caller's numbering) the vertices vert[3k..3k+2] of a mesh_c
+ * triangle containing it (mesh_c's caller numbering) and the barycentric
+ * weights w[3k..3k+2].  Used by lflts_run_field_pair to form the difference
+ * of a level pair's L2(D)-valued QoIs on the finer mesh (Sec. 4).
+ * Errors: LFLTS_ERR_ARG for null pointers, a bad mesh id, a vertex outside
+ * mesh_c or a non-finite weight; LFLTS_ERR_OOM / LFLTS_ERR_CUDA from the upload.
+ */
+int lflts_field_interp_add(lflts_ctx* ctx, int mesh_f, int mesh_c, const int32_t* vert,
+                           const double* w, int* interp_id);
+
+/*
+ * One level pair of the L2(D)-valued QoI u(., T) (Sec. 4: V = L2(D)): the
+ * fine and coarse solves of `job` (as lflts_run_pairs; the coarse one only
+ * when job->has_coarse), then for every draw s the difference on the fine
+ * mesh dU_s = u_l(., T) - I u_{l-1}(., T) (I: the interpolation interp_id,
+ * from job->coarse's mesh to job->fine's; ignored for level 0, dU_s = u_0)
+ * and in FP64 with compensated sums:
+ *   sum_dU    [n_nodes_f]  sum_s dU_s at every fine node (caller's order)
+ *   norm2     [S] or NULL  ||dU_s||^2 in L2(D), the exact integral of the P1
+ *                          function (consistent mass: |T|/12 (1 + delta_ab))
+ *   sum_norm2 [1]          sum_s ||dU_s||^2
+ * the sums of the V-valued estimator and its V-norm variance (Eqs.
+ * MLMCestimator and Vell_est).  job->dQ, Qf, sums may be NULL; when given
+ * they receive the scalar QoI of the same solves as in lflts_run_pairs.
+ * Memory kinds, streams and synchronisation as lflts_run_pairs.
+ * Errors: LFLTS_ERR_ARG for a bad job, a missing or mismatched interp_id;
+ * LFLTS_ERR_UNSTABLE (host mode) for a non-finite QoI or norm.
+ */
+int lflts_run_field_pair(lflts_ctx* ctx, const lflts_pair_job* job, int interp_id, double* sum_dU,
+                         double* norm2, double* sum_norm2, int mem, void* stream);
+
+/*
  * Gradient of the QoI with respect to the field parameters: for every draw
  * s, Q[s] (as lflts_solve) and dQdxi[s][k] = dQ/dxi_k, the exact derivative of
  * the computed (discrete) QoI.  Discrete adjoint of the u-form LF-LTS solve:

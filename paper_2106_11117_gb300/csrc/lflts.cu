@@ -23,6 +23,7 @@
 
 #include "../../include/lflts.h"
 #include "adjoint.cuh"
+#include "field_qoi.cuh"
 #include "inner_tile.cuh"
 #include "kernels.cuh"
 #include "mesh_prep.h"
@@ -54,6 +55,8 @@ struct MeshGPU {
   float* psi32 = nullptr;
   double* psi64 = nullptr;
   int* new2old = nullptr;
+  int* tri_dev = nullptr;    // caller's triangles and areas (L2(D)-valued QoI, uploaded on first use)
+  double* area_dev = nullptr;
   // coupling slots of R for the fused inner kernel (built on first use)
   int* rptr = nullptr;
   int2* rslot = nullptr;
@@ -85,6 +88,18 @@ struct Qoi {
   int nnz;
   int* idx = nullptr;  // new node ids
   double* g = nullptr;
+};
+
+// Nodal interpolation from a coarse to a fine mesh (caller's numbering).
+struct Interp {
+  int mesh_f, mesh_c;
+  int* vert = nullptr;   // [n_nodes_f][3] coarse vertices
+  double* w = nullptr;   // [n_nodes_f][3] barycentric weights
+};
+
+// Buffers of lflts_run_field_pair.
+struct FieldBufs {
+  Buf uf, uc, qf, qc, s1, n2, ps, pc, sums, xraw, dq;
 };
 
 // Largest solve (in kernels) captured into one CUDA graph.
@@ -165,6 +180,9 @@ struct lflts_ctx {
   int64_t tile_cap = 0;          // > 0: at most this many computed nodes per tile
   std::vector<void*> owned;  // device allocations of meshes, fields, QoIs
   std::unique_ptr<PairRun> run;  // lflts_run_pairs_slice: the run in progress, if any
+  std::vector<Interp> interps;   // lflts_field_interp_add
+  std::unique_ptr<Workspace> fws[2];  // fine and coarse solves of lflts_run_field_pair
+  std::unique_ptr<FieldBufs> fb;
   ~lflts_ctx();
 };
 
@@ -1792,15 +1810,22 @@ int lflts_destroy(lflts_ctx* c) {
     cudaDeviceSynchronize();
     for (auto& w : c->ws)
       for (auto& ge : w->graphs) cudaGraphExecDestroy(ge.exec);
+    for (auto& w : c->fws)
+      if (w)
+        for (auto& ge : w->graphs) cudaGraphExecDestroy(ge.exec);
     for (auto& w : c->ws)
       for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->W, &w->xipad, &w->xraw, &w->qps,
                      &w->qpc, &w->Q, &w->uN, &w->dts, &w->sig})
         if (b->p) cudaFree(b->p);
-    for (Workspace* w : {c->gws.get()})
+    for (Workspace* w : {c->gws.get(), c->fws[0].get(), c->fws[1].get()})
       if (w)
         for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->W, &w->xipad, &w->xraw, &w->qps,
                        &w->qpc, &w->Q, &w->uN, &w->dts, &w->sig})
           if (b->p) cudaFree(b->p);
+    if (c->fb)
+      for (Buf* b : {&c->fb->uf, &c->fb->uc, &c->fb->qf, &c->fb->qc, &c->fb->s1, &c->fb->n2, &c->fb->ps,
+                     &c->fb->pc, &c->fb->sums, &c->fb->xraw, &c->fb->dq})
+        if (b->p) cudaFree(b->p);
     if (c->gb)
       for (Buf* b : {&c->gb->ckpt, &c->gb->segU, &c->gb->rs, &c->gb->rho, &c->gb->gs, &c->gb->A, &c->gb->Aseg,
                      &c->gb->nua, &c->gb->nub, &c->gb->dnu, &c->gb->part, &c->gb->xraw, &c->gb->Q, &c->gb->G})
@@ -2093,6 +2118,130 @@ int lflts_run_pairs_slice(lflts_ctx* c, const lflts_pair_job* jobs, int n_jobs, 
   const int rf = pairs_finish(c, run, jobs, n_jobs, mem, st);
   c->run.reset();
   return rf;
+}
+
+int lflts_field_interp_add(lflts_ctx* c, int mesh_f, int mesh_c, const int32_t* vert, const double* w,
+                           int* interp_id) {
+  if (!c || !vert || !w || !interp_id) return LFLTS_ERR_ARG;
+  c->err.clear();
+  LF_TRY(set_device(c));
+  const int nm = static_cast<int>(c->meshes.size());
+  if (mesh_f < 0 || mesh_f >= nm || mesh_c < 0 || mesh_c >= nm)
+    return fail(c, LFLTS_ERR_ARG, "field_interp_add: bad mesh id");
+  const int64_t n_f = c->meshes[mesh_f]->h.n_nodes, n_c = c->meshes[mesh_c]->h.n_nodes;
+  for (int64_t k = 0; k < 3 * n_f; ++k) {
+    if (vert[k] < 0 || vert[k] >= n_c) return fail(c, LFLTS_ERR_ARG, "field_interp_add: vertex out of range");
+    if (!std::isfinite(w[k])) return fail(c, LFLTS_ERR_ARG, "field_interp_add: non-finite weight");
+  }
+  Interp in;
+  in.mesh_f = mesh_f;
+  in.mesh_c = mesh_c;
+  LF_TRY(upload(c, &in.vert, vert, size_t(3 * n_f)));
+  LF_TRY(upload(c, &in.w, w, size_t(3 * n_f)));
+  *interp_id = static_cast<int>(c->interps.size());
+  c->interps.push_back(in);
+  return LFLTS_OK;
+}
+
+int lflts_run_field_pair(lflts_ctx* c, const lflts_pair_job* jb, int interp_id, double* sum_dU, double* norm2,
+                         double* sum_norm2, int mem, void* stream) {
+  if (!c) return LFLTS_ERR_ARG;
+  c->err.clear();
+  LF_TRY(set_device(c));
+  if (!jb || !jb->xi || jb->S < 1 || jb->S > kMaxS || !sum_dU || !sum_norm2)
+    return fail(c, LFLTS_ERR_ARG, "run_field_pair: null job, xi, sum_dU or sum_norm2, or S out of range");
+  if (mem != LFLTS_MEM_HOST && mem != LFLTS_MEM_DEVICE) return fail(c, LFLTS_ERR_ARG, "run_field_pair: bad mem kind");
+  LF_TRY(check_desc(c, &jb->fine));
+  const Interp* in = nullptr;
+  if (jb->has_coarse) {
+    LF_TRY(check_desc(c, &jb->coarse));
+    if (interp_id < 0 || interp_id >= (int)c->interps.size() || c->interps[interp_id].mesh_f != jb->fine.mesh_id ||
+        c->interps[interp_id].mesh_c != jb->coarse.mesh_id)
+      return fail(c, LFLTS_ERR_ARG, "run_field_pair: interp_id does not map the coarse mesh to the fine mesh");
+    if (c->meshes[jb->coarse.mesh_id]->h.K != c->meshes[jb->fine.mesh_id]->h.K)
+      return fail(c, LFLTS_ERR_ARG, "run_field_pair: fine and coarse meshes have different K");
+    in = &c->interps[interp_id];
+  }
+  const int64_t S = jb->S;
+  MeshGPU& mf = *c->meshes[jb->fine.mesh_id];
+  const HostMesh& hf = mf.h;
+  const int64_t n_f = hf.n_nodes;
+  const int64_t n_c = in ? c->meshes[jb->coarse.mesh_id]->h.n_nodes : 0;
+  if (!mf.tri_dev) {
+    LF_TRY(upload(c, &mf.tri_dev, hf.tri.data(), hf.tri.size()));
+    LF_TRY(upload(c, &mf.area_dev, hf.area.data(), hf.area.size()));
+  }
+  for (auto& w : c->fws)
+    if (!w) w.reset(new Workspace());
+  if (!c->fb) c->fb.reset(new FieldBufs());
+  FieldBufs& fb = *c->fb;
+  const int chunk = 512;
+  const int64_t n_chunks = std::max<int64_t>(1, (hf.n_tri + chunk - 1) / chunk);
+  const int K = hf.K;
+  LF_TRY(ensure(c, fb.uf, size_t(n_f) * S * sizeof(double)));
+  if (in) LF_TRY(ensure(c, fb.uc, size_t(n_c) * S * sizeof(double)));
+  LF_TRY(ensure(c, fb.qf, size_t(S) * sizeof(double)));
+  LF_TRY(ensure(c, fb.qc, size_t(S) * sizeof(double)));
+  LF_TRY(ensure(c, fb.s1, size_t(n_f) * sizeof(double)));
+  LF_TRY(ensure(c, fb.n2, size_t(S) * sizeof(double)));
+  LF_TRY(ensure(c, fb.ps, size_t(n_chunks) * S * sizeof(double)));
+  LF_TRY(ensure(c, fb.pc, size_t(n_chunks) * S * sizeof(double)));
+  LF_TRY(ensure(c, fb.sums, 4 * sizeof(double)));
+  LF_TRY(ensure(c, fb.dq, size_t(S) * 2 * sizeof(double) + 4 * sizeof(double)));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LF_TRY(reset_bad(c, st));
+  const double* d_xi = jb->xi;
+  if (mem == LFLTS_MEM_HOST) {
+    LF_TRY(ensure(c, fb.xraw, size_t(S) * K * sizeof(double)));
+    LF_CUDA(c, cudaMemcpyAsync(fb.xraw.p, jb->xi, size_t(S) * K * sizeof(double), cudaMemcpyHostToDevice, st));
+    d_xi = static_cast<const double*>(fb.xraw.p);
+  }
+  double* uf = static_cast<double*>(fb.uf.p);
+  double* uc = in ? static_cast<double*>(fb.uc.p) : nullptr;
+  double* qf = static_cast<double*>(fb.qf.p);
+  double* qc = static_cast<double*>(fb.qc.p);
+  // the pair's solves with their final states gathered in the caller's node order (FP64)
+  LF_TRY(solve_device(c, jb->fine, d_xi, S, qf, uf, *c->fws[0], st));
+  if (in) LF_TRY(solve_device(c, jb->coarse, d_xi, S, qc, uc, *c->fws[1], st));
+  // dU = u_l - I u_{l-1} in place over uf, per-node sums over the draws
+  {
+    Prof pr(c, st);
+    const unsigned nb = static_cast<unsigned>((n_f + 7) / 8);
+    k_field_diff<<<nb, 256, 0, st>>>(n_f, (int)S, uf, uc, in ? in->vert : nullptr, in ? in->w : nullptr,
+                                     static_cast<double*>(fb.s1.p));
+    LF_CUDA(c, cudaGetLastError());
+    const int tb = static_cast<int>(std::min<int64_t>(S, 128));
+    k_field_norm_partial<<<dim3(static_cast<unsigned>(n_chunks), static_cast<unsigned>((S + tb - 1) / tb)), tb, 0,
+                           st>>>(hf.n_tri, (int)S, chunk, mf.tri_dev, mf.area_dev, uf, static_cast<double*>(fb.ps.p),
+                                 static_cast<double*>(fb.pc.p));
+    LF_CUDA(c, cudaGetLastError());
+    k_qoi_final<<<blocks_for(S, 128, 1 << 20), 128, 0, st>>>((int)n_chunks, (int)S, static_cast<double*>(fb.ps.p),
+                                                            static_cast<double*>(fb.pc.p),
+                                                            static_cast<double*>(fb.n2.p), c->d_bad);
+    LF_CUDA(c, cudaGetLastError());
+    k_level_sums<<<1, 256, 0, st>>>(S, static_cast<double*>(fb.n2.p), nullptr, static_cast<double*>(fb.sums.p));
+    LF_CUDA(c, cudaGetLastError());
+    pr.end(LFLTS_KERNEL_QOI, 8.0 * double(S) * (2.0 * n_f + 3.0 * n_c + 3.0 * hf.n_tri));
+    c->launches += 3;
+  }
+  // the scalar QoI of the same solves (dQ, Qf and level sums), when asked for
+  double* dq_buf = static_cast<double*>(fb.dq.p);
+  if (jb->dQ || jb->Qf || jb->sums) {
+    k_pair_diff<<<blocks_for(S, 128, 1 << 20), 128, 0, st>>>((int)S, qf, in ? qc : nullptr, dq_buf, dq_buf + S);
+    LF_CUDA(c, cudaGetLastError());
+    k_level_sums<<<1, 256, 0, st>>>(S, qf, in ? qc : nullptr, dq_buf + 2 * S);
+    LF_CUDA(c, cudaGetLastError());
+    c->launches += 2;
+  }
+  const cudaMemcpyKind kind = mem == LFLTS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  LF_CUDA(c, cudaMemcpyAsync(sum_dU, fb.s1.p, size_t(n_f) * sizeof(double), kind, st));
+  LF_CUDA(c, cudaMemcpyAsync(sum_norm2, fb.sums.p, sizeof(double), kind, st));
+  if (norm2) LF_CUDA(c, cudaMemcpyAsync(norm2, fb.n2.p, size_t(S) * sizeof(double), kind, st));
+  if (jb->dQ) LF_CUDA(c, cudaMemcpyAsync(jb->dQ, dq_buf, size_t(S) * sizeof(double), kind, st));
+  if (jb->Qf) LF_CUDA(c, cudaMemcpyAsync(jb->Qf, dq_buf + S, size_t(S) * sizeof(double), kind, st));
+  if (jb->sums) LF_CUDA(c, cudaMemcpyAsync(jb->sums, dq_buf + 2 * S, 4 * sizeof(double), kind, st));
+  if (mem == LFLTS_MEM_HOST) return check_bad(c, st);
+  return LFLTS_OK;
 }
 
 int lflts_grad_xi(lflts_ctx* c, const lflts_solve_desc* ds, const double* xi, int64_t S, int ckpt_every,

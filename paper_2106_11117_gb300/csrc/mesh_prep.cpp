@@ -58,6 +58,10 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
     area2[e] = d;
   }
 
+  m.tri.assign(tri, tri + 3 * n_tri);
+  m.area.resize(n_tri);
+  for (int64_t e = 0; e < n_tri; ++e) m.area[e] = 0.5 * area2[e];
+
   // ---- masks: P (free nodes only), R = vertices of elements touching P ----
   std::vector<uint8_t> inP(n_nodes, 0), inR(n_nodes, 0);
   if (P) {

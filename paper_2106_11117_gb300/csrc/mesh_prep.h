@@ -49,6 +49,8 @@ struct HostMesh {
   std::vector<double> minv;                // [n_free] 1 / m_i (lumped mass)
   std::vector<double> psi2;                // [n_tri][KP] psi * log2(e), zero padded
   std::vector<double> xy;                  // [n_nodes][2] coordinates, internal order
+  std::vector<int32_t> tri;                // [n_tri][3] vertices in the caller's numbering and order
+  std::vector<double> area;                // [n_tri] |T| in the caller's element order
 };
 
 // Coupling slots of the inner substeps on R, in the order the per-substep

@@ -38,7 +38,8 @@ EXPORTED = [
     "lflts_qoi_add", "lflts_solve", "lflts_level_sums", "lflts_run_pairs",
     "lflts_profile_enable", "lflts_profile_reset", "lflts_profile_read", "lflts_launch_count",
     "lflts_qoi_reduce_noalloc", "lflts_grad_xi", "lflts_set_option", "lflts_get_stats",
-    "lflts_source_add", "lflts_interp_weights", "lflts_run_pairs_slice",
+    "lflts_source_add", "lflts_interp_weights", "lflts_run_pairs_slice", "lflts_field_interp_add",
+    "lflts_run_field_pair",
 ]
 LFLTS_OPT_GRAPHS = 1
 LFLTS_OPT_AUTOTUNE = 2
@@ -111,6 +112,8 @@ def load(path: str | None = None):
         "lflts_level_sums": (i32, [vp, vp, vp, i64, vp, i32, vp]),
         "lflts_run_pairs": (i32, [vp, C.POINTER(PairJob), i32, i32, vp]),
         "lflts_run_pairs_slice": (i32, [vp, C.POINTER(PairJob), i32, i32, i32, i32, vp]),
+        "lflts_field_interp_add": (i32, [vp, i32, i32, vp, vp, C.POINTER(i32)]),
+        "lflts_run_field_pair": (i32, [vp, C.POINTER(PairJob), i32, vp, vp, vp, i32, vp]),
         "lflts_profile_enable": (i32, [vp, i32]),
         "lflts_profile_reset": (i32, [vp]),
         "lflts_profile_read": (i32, [vp, i32, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -278,6 +281,19 @@ def lflts_run_pairs_slice(ctx, jobs, slice, n_slices, mem=LFLTS_MEM_HOST, stream
     arr = jobs if isinstance(jobs, C.Array) else (PairJob * len(jobs))(*jobs)
     return _check(ctx, load().lflts_run_pairs_slice(ctx, arr, len(arr), int(mem), int(slice), int(n_slices),
                                                     stream))
+
+
+def lflts_field_interp_add(ctx, mesh_f, mesh_c, vert, w):
+    vert = np.ascontiguousarray(vert, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    iid = C.c_int()
+    _check(ctx, load().lflts_field_interp_add(ctx, int(mesh_f), int(mesh_c), _ptr(vert), _ptr(w), C.byref(iid)))
+    return iid.value
+
+
+def lflts_run_field_pair(ctx, job, interp_id, sum_dU, norm2, sum_norm2, mem=LFLTS_MEM_HOST, stream=None):
+    return _check(ctx, load().lflts_run_field_pair(ctx, C.byref(job), int(interp_id), _ptr(sum_dU), _ptr(norm2),
+                                                   _ptr(sum_norm2), int(mem), stream))
 
 
 def lflts_profile_enable(ctx, on=True):
