@@ -144,7 +144,7 @@ k_inner_tile(TileDev tp, MeshDev<Real> m, int S, const Real* __restrict__ W, con
                 for (int c = 0; c < VEC; ++c) rj.v[c] = Real(0);
               }
 #pragma unroll
-              for (int c = 0; c < VEC; ++c) acc[c] = couple(acc[c], w[j][q].v[c], rj.v[c], vi[c]);
+              for (int c = 0; c < VEC; ++c) acc[c] = couple(acc[c], w[j][q].v[c], Real(1), rj.v[c], vi[c]);
             }
           }
           const int nx = xp[j] & 15;
@@ -159,7 +159,7 @@ k_inner_tile(TileDev tp, MeshDev<Real> m, int S, const Real* __restrict__ W, con
               for (int c = 0; c < VEC; ++c) rj.v[c] = Real(0);
             }
 #pragma unroll
-            for (int c = 0; c < VEC; ++c) acc[c] = couple(acc[c], wo.v[c], rj.v[c], vi[c]);
+            for (int c = 0; c < VEC; ++c) acc[c] = couple(acc[c], wo.v[c], Real(1), rj.v[c], vi[c]);
           }
           Pack<Real, VEC> rn;
 #pragma unroll

@@ -152,20 +152,19 @@ struct Rn<double> {
   static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 };
 
-// One coupling term of a(P r_m)_i: acc + W_ij (r_j - v_i), r_j = 0 off P,
-// v_i = r_i on P (0 off P).
+// One coupling term of a(P r_m)_i: acc + W_ij (s r_j - v_i), r_j = 0 off P,
+// v_i = s r_i on P (0 off P), s the scale of the stored r_m.
 template <typename Real>
-__device__ __forceinline__ Real couple(Real acc, Real w, Real rj, Real vi) {
-  return Rn<Real>::fma(w, Rn<Real>::sub(rj, vi), acc);
+__device__ __forceinline__ Real couple(Real acc, Real w, Real s, Real rj, Real vi) {
+  return Rn<Real>::fma(w, Rn<Real>::fma(s, rj, -vi), acc);
 }
-// r_{m+1} = (1 + beta_m) r_m - beta_m r_{m-1} - c_m (g + m_i^-1 acc)
+// r_{m+1} = (1 + beta_m) r_m - beta_m r_{m-1} - c_m (g + m_i^-1 acc), with
+// r_m = src and r_{m-1} = srp
 template <typename Real>
-__device__ __forceinline__ Real inner_next(Real opb, Real rc, Real beta, Real rp, Real cm, Real gi, Real mi,
+__device__ __forceinline__ Real inner_next(Real opb, Real src, Real beta, Real srp, Real cm, Real gi, Real mi,
                                            Real acc) {
-  const Real a = Rn<Real>::mul(opb, rc);
-  const Real b = Rn<Real>::mul(beta, rp);
   const Real c = Rn<Real>::mul(cm, Rn<Real>::fma(mi, acc, gi));
-  return Rn<Real>::sub(Rn<Real>::sub(a, b), c);
+  return Rn<Real>::fma(opb, src, -Rn<Real>::fma(beta, srp, c));
 }
 
 // Thread -> (node row, sample vector) for blockDim.x = 256 threads.
@@ -346,14 +345,12 @@ k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
     const Pack<Real, VEC> rc = ldp<Real, VEC>(cur + is);
     const Pack<Real, VEC> gi = ldp<Real, VEC>(g + is);
     Pack<Real, VEC> rj[4], w[4], rp;
-    bool jc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = nb.j[q];
       const bool jP = j >= 0 && j < nP;
       // only P neighbours carry r; a P node also couples to its other neighbours
-      jc[q] = jP || (iP && j >= 0);  // a coupling slot (the others add nothing)
-      if (jc[q]) {
+      if (jP || (iP && j >= 0)) {
         w[q] = ldp<Real, VEC>(W + (size_t)nb.e[q] * S + s0);
       } else {
 #pragma unroll
@@ -380,10 +377,9 @@ k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
       acc[k] = Real(0);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (jc[q])
+    for (int q = 0; q < 4; ++q)  // a slot that does not couple has w = 0 and adds an exact zero
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] = couple(acc[k], w[q].v[k], Rn<Real>::mul(s_cur, rj[q].v[k]), vi[k]);
+      for (int k = 0; k < VEC; ++k) acc[k] = couple(acc[k], w[q].v[k], s_cur, rj[q].v[k], vi[k]);
     for (int t = t0; t < t1; ++t) {  // neighbours beyond the fourth (rare)
       const int2 o = m.adj[t];
       const bool jP = o.x < nP;
@@ -392,10 +388,10 @@ k_inner(MeshDev<Real> m, int S, int SB, const Real* __restrict__ W,
       if (jP) {
         const Pack<Real, VEC> ro = ldp<Real, VEC>(cur + (size_t)o.x * S + s0);
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] = couple(acc[k], wo.v[k], Rn<Real>::mul(s_cur, ro.v[k]), vi[k]);
+        for (int k = 0; k < VEC; ++k) acc[k] = couple(acc[k], wo.v[k], s_cur, ro.v[k], vi[k]);
       } else {
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] = couple(acc[k], wo.v[k], Rn<Real>::mul(s_cur, Real(0)), vi[k]);
+        for (int k = 0; k < VEC; ++k) acc[k] = couple(acc[k], wo.v[k], s_cur, Real(0), vi[k]);
       }
     }
     Pack<Real, VEC> rn;
@@ -523,7 +519,7 @@ k_inner_fused(MeshDev<Real> m, int S, int SBf, const Real* __restrict__ W, const
             for (int kk = 0; kk < VEC; ++kk) rj.v[kk] = Real(0);
           }
 #pragma unroll
-          for (int kk = 0; kk < VEC; ++kk) acc[kk] = couple(acc[kk], w.v[kk], Rn<Real>::mul(s_cur, rj.v[kk]), vi[kk]);
+          for (int kk = 0; kk < VEC; ++kk) acc[kk] = couple(acc[kk], w.v[kk], s_cur, rj.v[kk], vi[kk]);
         }
         const Real mi = sminv[i];
         Pack<Real, VEC> rn;

@@ -437,21 +437,28 @@ constexpr size_t kTileSmemMax = 220 * 1024;
 template <typename Real>
 cudaError_t tile_attr(int var, int smem) {
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  if (sizeof(Real) == 8) return cudaFuncSetAttribute(k_inner_tile<Real, 2, 3, 384>, attr, smem);
-  if (var == 0) return cudaFuncSetAttribute(k_inner_tile<Real, 4, 3, 384>, attr, smem);
-  return cudaFuncSetAttribute(k_inner_tile<Real, 2, 6, 384>, attr, smem);
+  if constexpr (sizeof(Real) == 8) {
+    (void)var;
+    return cudaFuncSetAttribute(k_inner_tile<Real, 2, 3, 384>, attr, smem);
+  } else {
+    if (var == 0) return cudaFuncSetAttribute(k_inner_tile<Real, 4, 3, 384>, attr, smem);
+    return cudaFuncSetAttribute(k_inner_tile<Real, 2, 6, 384>, attr, smem);
+  }
 }
 
 template <typename Real>
 void tile_launch(int var, int grid, size_t smem, cudaStream_t st, const TileDev& td, const MeshDev<Real>& md,
                  int S, const Real* W, const Real* g, const Real* u, Real* un, Real* d, const InnerCoef<Real>& k,
                  Real kappa) {
-  if (sizeof(Real) == 8)
+  if constexpr (sizeof(Real) == 8) {
+    (void)var;
     k_inner_tile<Real, 2, 3, 384><<<grid, 384, smem, st>>>(td, md, S, W, g, u, un, d, k, kappa);
-  else if (var == 0)
-    k_inner_tile<Real, 4, 3, 384><<<grid, 384, smem, st>>>(td, md, S, W, g, u, un, d, k, kappa);
-  else
-    k_inner_tile<Real, 2, 6, 384><<<grid, 384, smem, st>>>(td, md, S, W, g, u, un, d, k, kappa);
+  } else {
+    if (var == 0)
+      k_inner_tile<Real, 4, 3, 384><<<grid, 384, smem, st>>>(td, md, S, W, g, u, un, d, k, kappa);
+    else
+      k_inner_tile<Real, 2, 6, 384><<<grid, 384, smem, st>>>(td, md, S, W, g, u, un, d, k, kappa);
+  }
 }
 
 // One step of Alg. 2 for one batch (see kernels.cuh for the u-form): the
