@@ -2,24 +2,27 @@
 // large refined region, tile by tile, with the recursion on chip.
 //
 // The substeps touch only R and couple nodes only through P: r_{m+1} at a
-// node needs r_m at its P neighbours.  A tile is a spatially compact core of
-// R nodes plus p-1 layers of P nodes around it (layer k: the P neighbours of
-// layer k-1 not yet in the tile).  Substep m computes r_{m+1} on the core and
-// layers 1..p-1-m; after the last substep the core's values are exact, since
-// everything they depend on was computed inside the tile.  The outermost
-// layer only supplies r_1 = -c_0 g.  Halo nodes are computed redundantly by
-// every tile that holds them.
+// node needs r_m at its P neighbours.  A tile is a compact core of R nodes
+// (a square cell of R's bounding box) plus p-1 layers of P nodes around it
+// (layer k: the P neighbours of layer k-1 not yet in the tile).  Substep m
+// computes r_{m+1} on the core and layers 1..p-1-m; after the last substep
+// the core's values are exact, since everything they depend on was computed
+// inside the tile.  The outermost layer only supplies r_1 = -c_0 g.  Halo
+// nodes are computed again by every tile that holds them.
 //
 // One CTA takes a (tile, slab of VEC draws) work item.  Thread t owns the
 // tile nodes t, t + NT, ..., t + (IT-1) NT (one node and VEC draws each) and
-// keeps their g, r_m, r_{m-1}, coupling weights and neighbour slots in
+// keeps their g, r_m, r_{m-1}, coupling weights and neighbour rows in
 // registers for all substeps; shared memory holds only r_m of the tile for
-// the neighbours' reads (two planes, one per parity of m).  Per step and
-// node the global traffic is g once, the coupling weights once, and u, d in
-// and out on the core, instead of r_m, r_{m-1}, g, the weights and r_{m+1}
-// in every substep.  The arithmetic per node is that of k_inner term by term
+// the neighbours' reads (two planes, one per parity of m), plus one row of
+// zeros that the slots of neighbours off P (and unused slots, with weight 0)
+// point to, so the substep loop has no branches per slot.  Per step and node
+// the global traffic is g once, the coupling weights once, and u, d in and
+// out on the core, instead of r_m, r_{m-1}, g, the weights and r_{m+1} in
+// every substep.  The arithmetic per node is that of k_inner term by term
 // (same slots in the same order, same roundings, kernels.cuh), so the values
-// are the same bit for bit.
+// are the same bit for bit.  PC > 0 fixes p at compile time (the substep
+// loop unrolls); PC = 0 reads p from the coefficients.
 #pragma once
 #include "kernels.cuh"
 
@@ -27,37 +30,37 @@ namespace lflts {
 
 // Device view of a tile plan (built on the host, mesh_prep.h).
 struct TileDev {
-  const int* ptr;    // [n_tiles + 1] first tile node of every tile
-  const int* len;    // [n_tiles][p]: core size, then core + layers 1..k for k = 1..p-1
-  const int* node;   // mesh node of every tile node
-  const int2* sj;    // [tile node]: four coupling slots as 16-bit pairs (lo, hi) of
-                     //   (local neighbour, -1: a coupling without r (neighbour off P),
-                     //   -2: no slot)
-  const int4* se;    // [tile node]: edge ids of the four slots
-  const int* xp;     // [tile node]: (offset << 4) | count of the slots beyond the fourth
-  const int2* xs;    // those slots: (local neighbour or -1, edge id)
+  const int* ptr;        // [n_tiles + 1] first tile node of every tile
+  const int* len;        // [n_tiles][p]: core size, then core + layers 1..k for k = 1..p-1
+  const int* node;       // mesh node of every tile node
+  const int2* sj;        // [tile node]: local rows of the four slots as 16-bit pairs (lo, hi);
+                         //   row n_all (zeros) for a neighbour off P or an unused slot
+  const int4* se;        // [tile node]: edge ids of the four slots (-1: unused)
+  const int* xp;         // [tile node]: bit 0 node in P; (xp >> 1) & 15 slots beyond the
+                         //   fourth, from offset xp >> 5 in xs
+  const int2* xs;        // those slots: (local row, edge id)
+  const float* minv32;   // [tile node] 1 / m_i
+  const double* minv64;
   int n_tiles;
-  int n_all_max;     // largest tile (shared-memory planes)
+  int n_all_max;         // largest tile (shared-memory planes hold n_all_max + 1 rows)
 };
 
-__device__ __forceinline__ int slot_of(const int4& v, int q) {
-  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
-}
-// slot q of a node: the signed 16-bit half q % 2 of word q / 2
 __device__ __forceinline__ int slot_of(const int2& v, int q) {
   const int wd = (q < 2) ? v.x : v.y;
-  return (q & 1) ? (wd >> 16) : int(short(wd & 0xffff));
+  return (q & 1) ? int((unsigned)wd >> 16) : int(wd & 0xffff);
 }
+__device__ __forceinline__ float tile_minv(const TileDev& tp, int k, float) { return tp.minv32[k]; }
+__device__ __forceinline__ double tile_minv(const TileDev& tp, int k, double) { return tp.minv64[k]; }
 
-template <typename Real, int VEC, int IT, int NT>
+template <typename Real, int VEC, int IT, int NT, int PC>
 __global__ void __launch_bounds__(NT, 1)
-k_inner_tile(TileDev tp, MeshDev<Real> m, int S, const Real* __restrict__ W, const Real* __restrict__ g,
+k_inner_tile(TileDev tp, int S, const Real* __restrict__ W, const Real* __restrict__ g,
              const Real* __restrict__ u, Real* __restrict__ u_next, Real* __restrict__ d,
              const InnerCoef<Real> k, Real kappa) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* const plane0 = reinterpret_cast<Real*>(smem_raw);
-  Real* const plane1 = plane0 + (size_t)tp.n_all_max * VEC;
-  const int p = k.p;
+  Real* const plane1 = plane0 + (size_t)(tp.n_all_max + 1) * VEC;
+  const int p = PC > 0 ? PC : k.p;
   const int n_slabs = S / VEC;
   const int64_t n_work = (int64_t)tp.n_tiles * n_slabs;
   for (int64_t wk = blockIdx.x; wk < n_work; wk += gridDim.x) {
@@ -72,27 +75,25 @@ k_inner_tile(TileDev tp, MeshDev<Real> m, int S, const Real* __restrict__ W, con
     Pack<Real, VEC> rc[IT], rp[IT], gi[IT], w[IT][4];
     int2 sj[IT];
     Real mi[IT];
-    bool iP[IT];
     int xp[IT];
 #pragma unroll
     for (int j = 0; j < IT; ++j) {
       const int a = threadIdx.x + j * NT;
-      sj[j] = make_int2(int(0xfffefffe), int(0xfffefffe));  // four -2: no slot
+      sj[j] = make_int2(0, 0);
       xp[j] = 0;
       mi[j] = Real(0);
-      iP[j] = false;
       if (a < n_comp) {
         const int node = tp.node[base + a];
-        iP[j] = node < m.n_P;
-        mi[j] = m.minv[node];
+        mi[j] = tile_minv(tp, base + a, Real(0));
         sj[j] = tp.sj[base + a];
         xp[j] = tp.xp[base + a];
         const int4 se = tp.se[base + a];
         gi[j] = ldp<Real, VEC>(g + (size_t)node * S + s0);
+        const int e4[4] = {se.x, se.y, se.z, se.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          if (slot_of(sj[j], q) != -2) {
-            w[j][q] = ldp<Real, VEC>(W + (size_t)slot_of(se, q) * S + s0);
+          if (e4[q] >= 0) {
+            w[j][q] = ldp<Real, VEC>(W + (size_t)e4[q] * S + s0);
           } else {
 #pragma unroll
             for (int c = 0; c < VEC; ++c) w[j][q].v[c] = Real(0);
@@ -113,12 +114,17 @@ k_inner_tile(TileDev tp, MeshDev<Real> m, int S, const Real* __restrict__ W, con
       for (int c = 0; c < VEC; ++c) r1.v[c] = Rn<Real>::mul(k.neg_c0, r1.v[c]);
       stp<Real, VEC>(plane0 + (size_t)a * VEC, r1);
     }
+    if (threadIdx.x < VEC) {  // the zero row of both planes
+      plane0[(size_t)n_all * VEC + threadIdx.x] = Real(0);
+      plane1[(size_t)n_all * VEC + threadIdx.x] = Real(0);
+    }
     __syncthreads();
 
     // ---- substeps m = 1 .. p-1 ----------------------------------------------
-    const Real* cur = plane0;
-    Real* nxt = plane1;
+#pragma unroll(PC > 0 ? PC - 1 : 1)
     for (int mm = 1; mm < p; ++mm) {
+      const Real* cur = (mm & 1) ? plane0 : plane1;
+      Real* nxt = (mm & 1) ? plane1 : plane0;
       const bool last = (mm == p - 1);
       const int lm = len[p - 1 - mm];  // core and layers 1..p-1-m
       const Real opb = k.opb[mm], beta = k.beta[mm], cm = k.cm[mm];
@@ -126,38 +132,24 @@ k_inner_tile(TileDev tp, MeshDev<Real> m, int S, const Real* __restrict__ W, con
       for (int j = 0; j < IT; ++j) {
         const int a = threadIdx.x + j * NT;
         if (a < lm) {
+          const bool iP = xp[j] & 1;
           Real vi[VEC], acc[VEC];
 #pragma unroll
           for (int c = 0; c < VEC; ++c) {
-            vi[c] = iP[j] ? rc[j].v[c] : Real(0);
+            vi[c] = iP ? rc[j].v[c] : Real(0);
             acc[c] = Real(0);
           }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int sl = slot_of(sj[j], q);
-            if (sl != -2) {
-              Pack<Real, VEC> rj;
-              if (sl >= 0) {
-                rj = ldp<Real, VEC>(cur + (size_t)sl * VEC);
-              } else {
+          for (int q = 0; q < 4; ++q) {  // unused slots: weight 0 and the zero row
+            const Pack<Real, VEC> rj = ldp<Real, VEC>(cur + (size_t)slot_of(sj[j], q) * VEC);
 #pragma unroll
-                for (int c = 0; c < VEC; ++c) rj.v[c] = Real(0);
-              }
-#pragma unroll
-              for (int c = 0; c < VEC; ++c) acc[c] = couple(acc[c], w[j][q].v[c], Real(1), rj.v[c], vi[c]);
-            }
+            for (int c = 0; c < VEC; ++c) acc[c] = couple(acc[c], w[j][q].v[c], Real(1), rj.v[c], vi[c]);
           }
-          const int nx = xp[j] & 15;
-          for (int e = 0; e < nx; ++e) {  // slots beyond the fourth (a few nodes of graded fans)
-            const int2 o = tp.xs[(xp[j] >> 4) + e];
+          const int nx = (xp[j] >> 1) & 15;
+          for (int e = 0; e < nx; ++e) {  // slots beyond the fourth (nodes of the fans)
+            const int2 o = tp.xs[(xp[j] >> 5) + e];
             const Pack<Real, VEC> wo = ldp<Real, VEC>(W + (size_t)o.y * S + s0);
-            Pack<Real, VEC> rj;
-            if (o.x >= 0) {
-              rj = ldp<Real, VEC>(cur + (size_t)o.x * VEC);
-            } else {
-#pragma unroll
-              for (int c = 0; c < VEC; ++c) rj.v[c] = Real(0);
-            }
+            const Pack<Real, VEC> rj = ldp<Real, VEC>(cur + (size_t)o.x * VEC);
 #pragma unroll
             for (int c = 0; c < VEC; ++c) acc[c] = couple(acc[c], wo.v[c], Real(1), rj.v[c], vi[c]);
           }
@@ -184,9 +176,6 @@ k_inner_tile(TileDev tp, MeshDev<Real> m, int S, const Real* __restrict__ W, con
         }
       }
       __syncthreads();
-      const Real* tmp = cur;
-      cur = nxt;
-      nxt = const_cast<Real*>(tmp);
     }
   }
 }

@@ -429,36 +429,44 @@ int64_t tile_cap(const lflts_ctx* c, int var) {
   return c->tile_cap > 0 ? std::min<int64_t>(c->tile_cap, cap) : cap;
 }
 template <typename Real>
-size_t tile_smem(const TileDev& td, int var) {
-  return size_t(2) * size_t(td.n_all_max) * size_t(tile_shape<Real>(var).vec) * sizeof(Real);
+size_t tile_smem(const TileDev& td, int var) {  // two planes of n_all_max + 1 rows (the zero row)
+  return size_t(2) * size_t(td.n_all_max + 1) * size_t(tile_shape<Real>(var).vec) * sizeof(Real);
 }
 constexpr size_t kTileSmemMax = 220 * 1024;
 
-template <typename Real>
-cudaError_t tile_attr(int var, int smem) {
-  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  if constexpr (sizeof(Real) == 8) {
-    (void)var;
-    return cudaFuncSetAttribute(k_inner_tile<Real, 2, 3, 384>, attr, smem);
-  } else {
-    if (var == 0) return cudaFuncSetAttribute(k_inner_tile<Real, 4, 3, 384>, attr, smem);
-    return cudaFuncSetAttribute(k_inner_tile<Real, 2, 6, 384>, attr, smem);
-  }
+// Kernels of a tile shape and p (p = 4 and 8 compiled with the substep
+// loop unrolled, other p with a runtime loop).
+template <typename Real, int V, int IT, int PC>
+void tile_go(bool attr_only, int smem_attr, int grid, size_t smem, cudaStream_t st, const TileDev& td, int S,
+             const Real* W, const Real* g, const Real* u, Real* un, Real* d, const InnerCoef<Real>& k, Real kappa,
+             cudaError_t& e) {
+  if (attr_only)
+    e = cudaFuncSetAttribute(k_inner_tile<Real, V, IT, 384, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_attr);
+  else
+    k_inner_tile<Real, V, IT, 384, PC><<<grid, 384, smem, st>>>(td, S, W, g, u, un, d, k, kappa);
 }
-
+template <typename Real, int V, int IT>
+void tile_go_p(int p, bool attr_only, int smem_attr, int grid, size_t smem, cudaStream_t st, const TileDev& td,
+               int S, const Real* W, const Real* g, const Real* u, Real* un, Real* d, const InnerCoef<Real>& k,
+               Real kappa, cudaError_t& e) {
+  if (p == 8) tile_go<Real, V, IT, 8>(attr_only, smem_attr, grid, smem, st, td, S, W, g, u, un, d, k, kappa, e);
+  else if (p == 4) tile_go<Real, V, IT, 4>(attr_only, smem_attr, grid, smem, st, td, S, W, g, u, un, d, k, kappa, e);
+  else tile_go<Real, V, IT, 0>(attr_only, smem_attr, grid, smem, st, td, S, W, g, u, un, d, k, kappa, e);
+}
 template <typename Real>
-void tile_launch(int var, int grid, size_t smem, cudaStream_t st, const TileDev& td, const MeshDev<Real>& md,
-                 int S, const Real* W, const Real* g, const Real* u, Real* un, Real* d, const InnerCoef<Real>& k,
-                 Real kappa) {
+cudaError_t tile_call(int var, int p, bool attr_only, int smem_attr, int grid, size_t smem, cudaStream_t st,
+                      const TileDev& td, int S, const Real* W, const Real* g, const Real* u, Real* un, Real* d,
+                      const InnerCoef<Real>& k, Real kappa) {
+  cudaError_t e = cudaSuccess;
   if constexpr (sizeof(Real) == 8) {
     (void)var;
-    k_inner_tile<Real, 2, 3, 384><<<grid, 384, smem, st>>>(td, md, S, W, g, u, un, d, k, kappa);
+    tile_go_p<Real, 2, 3>(p, attr_only, smem_attr, grid, smem, st, td, S, W, g, u, un, d, k, kappa, e);
   } else {
-    if (var == 0)
-      k_inner_tile<Real, 4, 3, 384><<<grid, 384, smem, st>>>(td, md, S, W, g, u, un, d, k, kappa);
-    else
-      k_inner_tile<Real, 2, 6, 384><<<grid, 384, smem, st>>>(td, md, S, W, g, u, un, d, k, kappa);
+    if (var == 0) tile_go_p<Real, 4, 3>(p, attr_only, smem_attr, grid, smem, st, td, S, W, g, u, un, d, k, kappa, e);
+    else tile_go_p<Real, 2, 6>(p, attr_only, smem_attr, grid, smem, st, td, S, W, g, u, un, d, k, kappa, e);
   }
+  return e;
 }
 
 // One step of Alg. 2 for one batch (see kernels.cuh for the u-form): the
@@ -610,7 +618,7 @@ struct Stepper {
     }
     if (n_R > 0 && tvar >= 0 && !dts) {
       Prof pr(c, st);
-      tile_launch<Real>(tvar, tgrid, tsmem, st, tdev, md, (int)S, W, g, uc, un, d, coef, kappa);
+      tile_call<Real>(tvar, p, false, 0, tgrid, tsmem, st, tdev, (int)S, W, g, uc, un, d, coef, kappa);
       LF_CUDA(c, cudaGetLastError());
       // all substeps on chip: the outer-step bytes of R remain
       pr.end(LFLTS_KERNEL_INNER, 3.0 * n_R * Srb);
@@ -756,7 +764,11 @@ bool tile_ok(lflts_ctx* c, MeshGPU& mg, int n_R, int64_t S, int p, int var) {
       int* d_se = nullptr;
       int* d_xp = nullptr;
       int* d_xs = nullptr;
-      const bool up = !upload(c, &d_ptr, tp.ptr.data(), tp.ptr.size()) &&
+      float* d_m32 = nullptr;
+      double* d_m64 = nullptr;
+      const std::vector<float> m32(tp.minv.begin(), tp.minv.end());
+      const bool up = !upload(c, &d_m32, m32.data(), m32.size()) && !upload(c, &d_m64, tp.minv.data(), tp.minv.size()) &&
+                      !upload(c, &d_ptr, tp.ptr.data(), tp.ptr.size()) &&
                       !upload(c, &d_len, tp.len.data(), tp.len.size()) &&
                       !upload(c, &d_node, tp.node.data(), tp.node.size()) &&
                       !upload(c, &d_sj, tp.sj.data(), tp.sj.size()) &&
@@ -771,6 +783,8 @@ bool tile_ok(lflts_ctx* c, MeshGPU& mg, int n_R, int64_t S, int p, int var) {
         dt.dev.se = reinterpret_cast<const int4*>(d_se);
         dt.dev.xp = d_xp;
         dt.dev.xs = reinterpret_cast<const int2*>(d_xs);
+        dt.dev.minv32 = d_m32;
+        dt.dev.minv64 = d_m64;
         dt.dev.n_tiles = static_cast<int>(tp.ptr.size()) - 1;
         dt.dev.n_all_max = static_cast<int>(tp.n_all_max);
         dt.ok = true;
@@ -781,7 +795,9 @@ bool tile_ok(lflts_ctx* c, MeshGPU& mg, int n_R, int64_t S, int p, int var) {
   if (!it->second.ok) return false;
   const size_t smem = tile_smem<Real>(it->second.dev, var);
   if (smem > kTileSmemMax) return false;
-  return tile_attr<Real>(var, static_cast<int>(kTileSmemMax)) == cudaSuccess;
+  const InnerCoef<Real> k0{};
+  return tile_call<Real>(var, p, true, static_cast<int>(kTileSmemMax), 0, 0, nullptr, it->second.dev, 0, nullptr,
+                         nullptr, nullptr, nullptr, nullptr, k0, Real(0)) == cudaSuccess;
 }
 
 // Draw segments of a ragged batch: draws [off, off + cnt) take n_steps steps

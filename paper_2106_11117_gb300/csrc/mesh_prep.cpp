@@ -416,46 +416,77 @@ void tile_nodes(const HostMesh& m, const std::vector<int32_t>& order, int64_t a0
 
 bool build_tile_plan(const HostMesh& m, int p, int64_t cap, TilePlan& out) {
   out = TilePlan();
-  const int64_t nR = m.n_R;
+  const int64_t nR = m.n_R, nP = m.n_P;
   if (nR == 0 || p < 2 || cap < 16) return false;
   std::vector<int32_t> rptr, rsj, rse;
   build_r_slots(m, rptr, rsj, rse);
-  const std::vector<int32_t> order = morton_order_R(m);
-  std::vector<int64_t> stamp(std::max<int64_t>(m.n_free, nR), -1);
+  const std::vector<int32_t> order = morton_order_R(m);  // Morton order inside each cell
+  double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+  for (int64_t i = 0; i < nR; ++i) {
+    x0 = std::min(x0, m.xy[2 * i]);
+    x1 = std::max(x1, m.xy[2 * i]);
+    y0 = std::min(y0, m.xy[2 * i + 1]);
+    y1 = std::max(y1, m.xy[2 * i + 1]);
+  }
+  const double wx = std::max(x1 - x0, 1e-300), wy = std::max(y1 - y0, 1e-300);
+  // nodes per unit length if R filled its box; the core of a cell of side L
+  // holds about (L / h)^2 nodes and its tile (L / h + 2 (p - 2))^2
+  const double h = std::sqrt(wx * wy / double(nR));
+  double L = std::max(h, (std::sqrt(double(cap)) - 2.0 * (p - 2)) * h);
+  std::vector<int64_t> stamp(nR, -1);
   std::vector<int32_t> nodes, lens;
+  std::vector<std::vector<int32_t>> cells;
   int64_t mark = 0;
-  // core size: shrink until the computed part (core + layers 1..p-2) of
-  // every tile fits `cap`
-  int64_t core = std::min<int64_t>(nR, std::max<int64_t>(1, cap / 2));
   for (int attempt = 0;; ++attempt) {
-    const int64_t n_tiles = (nR + core - 1) / core;
+    // cores: the nodes of R binned into cells of side L (each in Morton order)
+    const int64_t ncx = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(wx / L))),
+                  ncy = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(wy / L)));
+    if (ncx * ncy > (int64_t(1) << 26)) return false;
+    std::vector<int32_t> cell_of(nR);
+    for (int64_t a = 0; a < nR; ++a) {
+      const int32_t i = order[a];
+      const int64_t cx = std::min<int64_t>(ncx - 1, static_cast<int64_t>((m.xy[2 * i] - x0) / L));
+      const int64_t cy = std::min<int64_t>(ncy - 1, static_cast<int64_t>((m.xy[2 * i + 1] - y0) / L));
+      // cells in row order, so that consecutive tiles are neighbours
+      cell_of[i] = static_cast<int32_t>(cy * ncx + cx);
+    }
+    cells.clear();
+    std::vector<std::vector<int32_t>> byc(ncx * ncy);
+    for (int64_t a = 0; a < nR; ++a) byc[cell_of[order[a]]].push_back(order[a]);
+    for (auto& v : byc)
+      if (!v.empty()) cells.push_back(std::move(v));
     int64_t worst = 0;
-    for (int64_t t = 0; t < n_tiles; ++t) {
-      tile_nodes(m, order, t * nR / n_tiles, (t + 1) * nR / n_tiles, p - 1, stamp, mark++, nodes, lens);
+    for (const auto& core : cells) {
+      tile_nodes(m, core, 0, static_cast<int64_t>(core.size()), p - 1, stamp, mark++, nodes, lens);
       worst = std::max<int64_t>(worst, lens[p - 2]);
-      if (lens[p - 1] > 32767) return false;
+      if (lens[p - 1] > 32000) {
+        worst = cap + 1;
+        break;
+      }
     }
     if (worst <= cap) break;
-    if (core == 1 || attempt > 60) return false;
-    core = std::max<int64_t>(1, std::min<int64_t>(core - 1, static_cast<int64_t>(core * 0.95 * double(cap) / double(worst))));
+    if (attempt > 80 || L <= 0.5 * h) return false;
+    L *= 0.95;
   }
-  const int64_t n_tiles = (nR + core - 1) / core;
   out.p = p;
   out.cap = static_cast<int>(cap);
   out.ptr.assign(1, 0);
-  std::vector<int32_t> local(std::max<int64_t>(m.n_free, nR), -1);
-  for (int64_t t = 0; t < n_tiles; ++t) {
-    tile_nodes(m, order, t * nR / n_tiles, (t + 1) * nR / n_tiles, p - 1, stamp, mark, nodes, lens);
-    for (size_t a = 0; a < nodes.size(); ++a) local[nodes[a]] = static_cast<int32_t>(a);
+  std::vector<int32_t> local(nR, -1);
+  for (const auto& core : cells) {
+    tile_nodes(m, core, 0, static_cast<int64_t>(core.size()), p - 1, stamp, mark, nodes, lens);
+    const int32_t n_all = static_cast<int32_t>(nodes.size());
+    for (int32_t a = 0; a < n_all; ++a) local[nodes[a]] = a;
     const int32_t n_comp = lens[p - 2];
-    for (size_t a = 0; a < nodes.size(); ++a) {
+    for (int32_t a = 0; a < n_all; ++a) {
       const int32_t i = nodes[a];
       out.node.push_back(i);
-      int32_t q4[4] = {-2, -2, -2, -2}, e4[4] = {0, 0, 0, 0};
+      // slots: local row of the neighbour's r, or the zero row (n_all) for a
+      // coupling to a node off P; unused slots: zero row and edge -1
+      int32_t q4[4] = {n_all, n_all, n_all, n_all}, e4[4] = {-1, -1, -1, -1};
       int32_t xoff = static_cast<int32_t>(out.xs.size() / 2), xcnt = 0;
-      if (static_cast<int32_t>(a) < n_comp) {
+      if (a < n_comp) {
         for (int32_t s = rptr[i]; s < rptr[i + 1]; ++s) {
-          int32_t lj = -1;
+          int32_t lj = n_all;
           if (rsj[s] >= 0) {
             if (stamp[rsj[s]] != mark) return false;  // cannot happen: the layers close the tile
             lj = local[rsj[s]];
@@ -472,13 +503,14 @@ bool build_tile_plan(const HostMesh& m, int p, int64_t cap, TilePlan& out) {
         }
         if (xcnt > 15) return false;
       }
-      out.sj.push_back(static_cast<int32_t>((uint32_t(uint16_t(q4[0]))) | (uint32_t(uint16_t(q4[1])) << 16)));
-      out.sj.push_back(static_cast<int32_t>((uint32_t(uint16_t(q4[2]))) | (uint32_t(uint16_t(q4[3])) << 16)));
+      out.sj.push_back(static_cast<int32_t>(uint32_t(uint16_t(q4[0])) | (uint32_t(uint16_t(q4[1])) << 16)));
+      out.sj.push_back(static_cast<int32_t>(uint32_t(uint16_t(q4[2])) | (uint32_t(uint16_t(q4[3])) << 16)));
       for (int q = 0; q < 4; ++q) out.se.push_back(e4[q]);
-      out.xp.push_back(xcnt ? ((xoff << 4) | xcnt) : 0);
+      out.xp.push_back((xcnt ? ((xoff << 5) | (xcnt << 1)) : 0) | (i < nP ? 1 : 0));
+      out.minv.push_back(i < m.n_free ? m.minv[i] : 0.0);
     }
     for (int k = 0; k < p; ++k) out.len.push_back(lens[k]);
-    out.n_all_max = std::max<int64_t>(out.n_all_max, static_cast<int64_t>(nodes.size()));
+    out.n_all_max = std::max<int64_t>(out.n_all_max, static_cast<int64_t>(n_all));
     out.ptr.push_back(static_cast<int32_t>(out.node.size()));
     ++mark;
   }

@@ -62,27 +62,32 @@ struct HostMesh {
 void build_r_slots(const HostMesh& m, std::vector<int32_t>& ptr, std::vector<int32_t>& slot_j,
                    std::vector<int32_t>& slot_e);
 
-// Tiles of the on-chip inner substeps (k_inner_tile).  Tile t holds the
-// nodes node[ptr[t] .. ptr[t+1]): a core of R nodes (a Morton-contiguous
-// range of R), then p-1 layers of P nodes, layer k being the P neighbours of
-// layer k-1 that are not in the tile yet.  len[t*p + k] = core + layers 1..k
-// (k = 0..p-1).  Substep m computes the prefix len[p-1-m]; the first
-// len[p-2] nodes (at most `cap`) are the computed ones.  For every tile node
-// the first four coupling slots of the per-substep kernel's visiting order
-// (build_r_slots) as (local neighbour index, -1 for a neighbour off P, -2
-// for no slot) in 16-bit halves of sj[2 a], sj[2 a + 1], their edge ids in
-// se[4 a + q], and the slots beyond the fourth in xs as (local or -1, edge)
-// pairs from offset xp[a] >> 4, count xp[a] & 15.
+// Tiles of the on-chip inner substeps (k_inner_tile).  The cores are the
+// nodes of R binned into square cells of R's bounding box (each cell's nodes
+// in Morton order); tile t holds node[ptr[t] .. ptr[t+1]): its core, then
+// p-1 layers of P nodes, layer k being the P neighbours of layer k-1 that are
+// not in the tile yet.  len[t*p + k] = core + layers 1..k (k = 0..p-1).
+// Substep m computes the prefix len[p-1-m]; the first len[p-2] nodes (at
+// most `cap`) are the computed ones.  The cell side is the largest (in steps
+// of 5 %) for which every tile fits `cap`.  For every tile node a: the first
+// four coupling slots of the per-substep kernel's visiting order
+// (build_r_slots) as local rows in 16-bit halves of sj[2 a], sj[2 a + 1]
+// (the row n_all of the tile, one past its last node, stands for a neighbour
+// off P and for an unused slot: the kernel keeps zeros there), their edge
+// ids in se[4 a + q] (-1: unused slot), the slots beyond the fourth in xs as
+// (local row, edge) pairs from offset xp[a] >> 5, count (xp[a] >> 1) & 15,
+// bit 0 of xp[a] set for a node in P, and minv[a] = 1 / m_i.
 struct TilePlan {
   int p = 0, cap = 0;
   int64_t n_all_max = 0;               // largest tile
   std::vector<int32_t> ptr, len, node;
   std::vector<int32_t> sj, se, xp, xs;
+  std::vector<double> minv;
 };
 
 // Build the plan for tiles of at most `cap` computed nodes; false (and an
-// empty plan) when R is empty, p < 2, a tile would exceed 32767 nodes or a
-// node has more than 15 slots beyond the fourth.
+// empty plan) when R is empty, p < 2, a tile would exceed 32000 nodes, no
+// cell size fits or a node has more than 15 slots beyond the fourth.
 bool build_tile_plan(const HostMesh& m, int p, int64_t cap, TilePlan& out);
 
 // Nodal interpolation between two triangulations of one domain: for every
