@@ -499,6 +499,69 @@ def _classes_json(prof):
             for k, v in prof.items() if v["launches"]}
 
 
+def _alg1_run(lflts, mlmc, ctx, hs, cfg, eps, plain, L_max, n_init, seed_off=0):
+    """Alg. 1 on the given level handles with the workload's draws; wall time."""
+    from workload import xi_uniform
+
+    def w(h):
+        return h.n_steps * (h.info["n_free"] + h.p * h.info["n_R"])
+
+    def cost(l):
+        return float(w(hs[l]) + (w(hs[l - 1]) if l else 0))
+
+    def draw(l, off, n):
+        return xi_uniform(cfg.seed + seed_off, l, n, cfg.K, offset=off)
+
+    ev = mlmc.GpuLevelPairs(lflts, ctx, hs, precision=32, plain=plain)
+    r = mlmc.alg1(ev, draw, eps, cost, lambda l: n_init, L_max=L_max)
+    return {"seconds": r.seconds, "estimate": r.estimate, "L": r.L, "N": r.N,
+            "rmse_estimate": math.sqrt(r.mse), "V": r.V, "bias": r.bias, "calls": ev.calls,
+            "dtype": "f64" if plain else "f32", "work_units": r.cost}
+
+
+def run_tte(args):
+    """MLMC (Alg. 1) to RMSE eps on the batched hierarchies (Sec. 2.2, Alg. 1,
+    Eq. optimal_Nl): (1) the bandwidth hierarchy square1024-p4-K8 (128^2 ..
+    1024^2 base cells, p = 4) to eps = --eps-bw with the batched FP32 path;
+    (2) the first levels of square128-p8-K8 (128^2 .. 512^2 base cells, p = 8)
+    to eps = --eps-cls with the batched FP32 path and with the plain per-draw
+    FP64 path (one draw per call) on the same draws.  Wall time of the whole
+    Alg. 1 (mesh setup excluded), estimates and their difference."""
+    import torch
+    from paper_2106_11117_gb300 import build, lflts, mlmc
+    from workload import CONFIG_BANDWIDTH, CONFIG_BATCHED, level_problem
+    build.build()
+    torch.cuda.set_device(0)
+    out = {"mode": "time_to_eps", "metric": "MLMC time to RMSE eps (Alg. 1)", "unit": "s",
+           "higher_is_better": False, "n_gpus": 1, "data": "synthetic"}
+    ctx = lflts.Context(0)
+    try:
+        if not args.tte_skip_bw:
+            hs = [ctx.add_level(level_problem(CONFIG_BANDWIDTH, l)) for l in range(CONFIG_BANDWIDTH.levels)]
+            r = _alg1_run(lflts, mlmc, ctx, hs, CONFIG_BANDWIDTH, args.eps_bw, False,
+                          CONFIG_BANDWIDTH.levels - 1, args.tte_n_init)
+            out["bandwidth_hierarchy"] = {"workload": CONFIG_BANDWIDTH.name + " (128^2..1024^2, p=4, K=8)",
+                                          "eps": args.eps_bw, "batched_fp32": r}
+        cfg = CONFIG_BATCHED
+        L_max = args.tte_levels - 1
+        hs = [ctx.add_level(level_problem(cfg, l)) for l in range(args.tte_levels)]
+        res = {}
+        for name, plain in (("batched_fp32", False), ("plain_fp64", True)):
+            if plain and args.tte_skip_plain:
+                continue
+            res[name] = _alg1_run(lflts, mlmc, ctx, hs, cfg, args.eps_cls, plain, L_max, args.tte_n_init)
+        blk = {"workload": f"{cfg.name} levels 0..{L_max} (128^2..{128 * 2 ** L_max}^2, p=8, K=8)",
+               "eps": args.eps_cls, **res}
+        if "plain_fp64" in res:
+            blk["speedup"] = res["plain_fp64"]["seconds"] / res["batched_fp32"]["seconds"]
+            blk["estimate_diff"] = abs(res["plain_fp64"]["estimate"] - res["batched_fp32"]["estimate"])
+            blk["estimate_diff_over_eps"] = blk["estimate_diff"] / args.eps_cls
+        out["batched_hierarchy"] = blk
+    finally:
+        ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_lshape(args):
     """Uneven batching on the graded L-shape (lshape-graded-s2-K16-ricker):
     4 levels (m = 58..464 layers, p = 3, 5, 9, 17), Gaussian draws with their
@@ -790,8 +853,14 @@ def main():
     ap.add_argument("--slices", type=int, default=20,
                     help="time slices per level-pair batch (one bench step = one slice)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["batched", "plain", "bandwidth", "lshape", "adjoint"],
+    ap.add_argument("--config", choices=["batched", "plain", "bandwidth", "lshape", "adjoint", "tte"],
                     default="batched")
+    ap.add_argument("--eps-bw", type=float, default=1e-3, help="RMSE target on the bandwidth hierarchy")
+    ap.add_argument("--eps-cls", type=float, default=2e-3, help="RMSE target, batched vs plain comparison")
+    ap.add_argument("--tte-levels", type=int, default=3, help="levels of square128-p8-K8 in the comparison")
+    ap.add_argument("--tte-n-init", type=int, default=64, help="initial samples per level of Alg. 1")
+    ap.add_argument("--tte-skip-plain", action="store_true")
+    ap.add_argument("--tte-skip-bw", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cores", type=int, default=0)
@@ -816,6 +885,8 @@ def main():
         run_lshape(args)
     elif args.config == "adjoint":
         run_adjoint(args)
+    elif args.config == "tte":
+        run_tte(args)
     else:
         run_ours(args)
 

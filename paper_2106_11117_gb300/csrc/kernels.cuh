@@ -153,10 +153,12 @@ struct Rn<double> {
 };
 
 // One coupling term of a(P r_m)_i: acc + W_ij (s r_j - v_i), r_j = 0 off P,
-// v_i = s r_i on P (0 off P), s the scale of the stored r_m.
+// v_i = s r_i on P (0 off P), s the scale of the stored r_m; s r_j is
+// rounded on its own, so that a kernel that stores r_m = s r_j already
+// scaled (s = 1) gets the same values.
 template <typename Real>
 __device__ __forceinline__ Real couple(Real acc, Real w, Real s, Real rj, Real vi) {
-  return Rn<Real>::fma(w, Rn<Real>::fma(s, rj, -vi), acc);
+  return Rn<Real>::fma(w, Rn<Real>::sub(Rn<Real>::mul(s, rj), vi), acc);
 }
 // r_{m+1} = (1 + beta_m) r_m - beta_m r_{m-1} - c_m (g + m_i^-1 acc), with
 // r_m = src and r_{m-1} = srp
