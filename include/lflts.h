@@ -86,8 +86,7 @@ enum {
                                  R (a compact core plus p-1 layers of P nodes, recomputed by the
                                  neighbouring tiles) with each node's state in registers and r_m in
                                  shared memory; same results bit for bit, uniform batches only:
-                                 0 never; 1 (default) autotuned where |R| > 2048; 2 always (first
-                                 tile shape); 3 always (second tile shape, FP32) */
+                                 0 never; 1 (default) autotuned where |R| > 2048; 2 always */
   LFLTS_OPT_TILE_CAP = 7      /* 0 (default): tiles as large as the kernel's registers allow; n >= 16:
                                  at most n computed nodes per tile (more, smaller tiles) */
 };
@@ -421,7 +420,7 @@ int lflts_launch_count(lflts_ctx* ctx, int64_t* launches);
 
 /* Set an LFLTS_OPT_* option of the context.
  * Errors: LFLTS_ERR_ARG for a NULL context, an unknown option, a fused-inner mode
- * outside {0, 1, 2}, a tiled-inner mode outside {0, .., 3} or a tile capacity
+ * outside {0, 1, 2}, a tiled-inner mode outside {0, 1, 2} or a tile capacity
  * in [1, 15] or negative. */
 int lflts_set_option(lflts_ctx* ctx, int option, int64_t value);
 

@@ -176,7 +176,7 @@ struct lflts_ctx {
   bool graphs = true;
   bool autotune = true;
   int fused_mode = 1;            // fused inner kernel: 0 never, 1 autotuned, 2 always where it fits
-  int tile_mode = 1;             // tiled inner kernel: 0 never, 1 autotuned, 2/3 always (first/second shape)
+  int tile_mode = 1;             // tiled inner kernel: 0 never, 1 autotuned, 2 always where it fits
   int64_t tile_cap = 0;          // > 0: at most this many computed nodes per tile
   std::vector<void*> owned;  // device allocations of meshes, fields, QoIs
   std::unique_ptr<PairRun> run;  // lflts_run_pairs_slice: the run in progress, if any
@@ -415,12 +415,12 @@ struct TileShape {
 };
 template <typename Real>
 int tile_shapes() {
-  return sizeof(Real) == 4 ? 2 : 1;
+  return 1;
 }
 template <typename Real>
-TileShape tile_shape(int var) {
+TileShape tile_shape(int) {  // one 16-byte row per node and slab
   if (sizeof(Real) == 8) return {2, 3, 384};
-  return var == 0 ? TileShape{4, 3, 384} : TileShape{2, 6, 384};
+  return TileShape{4, 3, 384};
 }
 template <typename Real>
 int64_t tile_cap(const lflts_ctx* c, int var) {
@@ -429,8 +429,8 @@ int64_t tile_cap(const lflts_ctx* c, int var) {
   return c->tile_cap > 0 ? std::min<int64_t>(c->tile_cap, cap) : cap;
 }
 template <typename Real>
-size_t tile_smem(const TileDev& td, int var) {  // two planes of n_all_max + 1 rows (the zero row)
-  return size_t(2) * size_t(td.n_all_max + 1) * size_t(tile_shape<Real>(var).vec) * sizeof(Real);
+size_t tile_smem(const TileDev& td, int var) {
+  return tile_smem_layout(td.n_all_max, td.comp_max, td.core_max, tile_shape<Real>(var).vec, sizeof(Real)).total;
 }
 constexpr size_t kTileSmemMax = 220 * 1024;
 
@@ -463,8 +463,8 @@ cudaError_t tile_call(int var, int p, bool attr_only, int smem_attr, int grid, s
     (void)var;
     tile_go_p<Real, 2, 3>(p, attr_only, smem_attr, grid, smem, st, td, S, W, g, u, un, d, k, kappa, e);
   } else {
-    if (var == 0) tile_go_p<Real, 4, 3>(p, attr_only, smem_attr, grid, smem, st, td, S, W, g, u, un, d, k, kappa, e);
-    else tile_go_p<Real, 2, 6>(p, attr_only, smem_attr, grid, smem, st, td, S, W, g, u, un, d, k, kappa, e);
+    (void)var;
+    tile_go_p<Real, 4, 3>(p, attr_only, smem_attr, grid, smem, st, td, S, W, g, u, un, d, k, kappa, e);
   }
   return e;
 }
@@ -541,8 +541,14 @@ struct Stepper {
         tvar = kind - 3;
         tdev = it->second.dev;
         tsmem = tile_smem<Real>(tdev, tvar);
-        const int64_t work = int64_t(tdev.n_tiles) * (S / tile_shape<Real>(tvar).vec);
-        tgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(work, c->sms)));
+        // work units of a tile and a run of slabs, at least two per SM
+        const int64_t n_slabs = S / tile_shape<Real>(tvar).vec;
+        const int64_t chunks = std::max<int64_t>(
+            1, std::min<int64_t>(n_slabs, (2 * int64_t(c->sms) + tdev.n_tiles - 1) / tdev.n_tiles));
+        tdev.chunk = static_cast<int>((n_slabs + chunks - 1) / chunks);
+        tdev.chunks = static_cast<int>((n_slabs + tdev.chunk - 1) / tdev.chunk);
+        const int64_t units = int64_t(tdev.n_tiles) * tdev.chunks;
+        tgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(units, c->sms)));
       }
     }
     if (kind >= 2 && n_R > 0 && p > 1 && p <= 64) {
@@ -787,6 +793,13 @@ bool tile_ok(lflts_ctx* c, MeshGPU& mg, int n_R, int64_t S, int p, int var) {
         dt.dev.minv64 = d_m64;
         dt.dev.n_tiles = static_cast<int>(tp.ptr.size()) - 1;
         dt.dev.n_all_max = static_cast<int>(tp.n_all_max);
+        int comp_max = 0, core_max = 0;
+        for (int t = 0; t < dt.dev.n_tiles; ++t) {
+          comp_max = std::max(comp_max, tp.len[size_t(t) * p + p - 2]);
+          core_max = std::max(core_max, tp.len[size_t(t) * p]);
+        }
+        dt.dev.comp_max = comp_max;
+        dt.dev.core_max = core_max;
         dt.ok = true;
       }
     }
@@ -2349,7 +2362,7 @@ int lflts_set_option(lflts_ctx* c, int option, int64_t value) {
       for (auto& m : c->meshes) m->tuned.clear();  // re-tune with the new candidate set
       return LFLTS_OK;
     case LFLTS_OPT_TILED_INNER:
-      if (value < 0 || value > 3) return fail(c, LFLTS_ERR_ARG, "set_option: tiled inner mode must be 0..3");
+      if (value < 0 || value > 2) return fail(c, LFLTS_ERR_ARG, "set_option: tiled inner mode must be 0, 1 or 2");
       c->tile_mode = static_cast<int>(value);
       for (auto& m : c->meshes) m->tuned.clear();
       return LFLTS_OK;

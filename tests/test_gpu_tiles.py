@@ -3,7 +3,7 @@ launch, tile by tile (a compact core of R plus p-1 layers of P nodes, the
 halo recomputed by neighbouring tiles), node state in registers.  Its values
 must equal those of one launch per substep bit for bit -- same slots, same
 order, same roundings -- for every tile size (small capacities force many
-tiles and halos that cross tile borders), both tile shapes, FP32 and FP64,
+tiles and halos that cross tile borders), FP32 and FP64,
 p = 2..9, with a point source; and on a full-size mesh of the benchmark
 hierarchy it must agree with the FP64 oracle over a short horizon."""
 import numpy as np
@@ -49,7 +49,7 @@ def test_tiled_inner_kernel_bit_identical(lf, prec, p):
     xi = draws(40, 4, seed=200 + p)
     Q0, U0, l0, h = _solve(lf, lev, xi, prec, 0)
     assert h.info["n_R"] > 64
-    modes = (2, 3) if prec == 32 else (2,)
+    modes = (2,)
     # capacities that still hold a core plus p - 2 computed layers (smaller
     # ones make no plan and the per-substep path runs)
     caps = {2: (0, 64, 16), 3: (0, 64, 16), 5: (0, 200, 64), 9: (0, 600)}[p]
@@ -69,7 +69,7 @@ def test_tiled_inner_kernel_fans_and_autotune(lf):
     lev = small_level(n=20, p=4, K=4, box=(0.3, 0.62, 0.33, 0.71))
     xi = draws(24, 4, seed=9)
     Q0, U0, _, _ = _solve(lf, lev, xi, 32, 0)
-    for mode, cap, tune in ((2, 40, 0), (3, 40, 0), (1, 0, 1), (2, 0, 1)):
+    for mode, cap, tune in ((2, 40, 0), (1, 0, 1), (2, 0, 1)):
         Q, U, _, _ = _solve(lf, lev, xi, 32, mode, cap, tune)
         np.testing.assert_array_equal(U, U0)
         np.testing.assert_array_equal(Q, Q0)
