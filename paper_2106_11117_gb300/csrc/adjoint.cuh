@@ -244,12 +244,11 @@ __global__ void k_adj_seed(int nnz, int S, const int* __restrict__ idx, const do
 template <int KP>
 __global__ void __launch_bounds__(128)
 k_grad_contract(int64_t n_edges, int S, int64_t chunk, const int2* __restrict__ ee, const double* __restrict__ eg,
-                const double* __restrict__ psi2, const double* __restrict__ xi, int K,
+                const double* __restrict__ psi, const double* __restrict__ xi, int K,
                 const double* __restrict__ A, double* __restrict__ part) {
   const int s = blockIdx.y * blockDim.x + threadIdx.x;
   if (s >= S) return;
   const int c = blockIdx.x;
-  const double inv_log2e = 0.69314718055994530942;  // psi = psi2 / log2(e)
   double xr[KP];
 #pragma unroll
   for (int k = 0; k < KP; ++k) xr[k] = k < K ? xi[(size_t)s * K + k] : 0.0;
@@ -264,11 +263,11 @@ k_grad_contract(int64_t n_edges, int S, int64_t chunk, const int2* __restrict__ 
     for (int side = 0; side < 2; ++side) {
       const int t = side ? el.y : el.x;
       if (t < 0) continue;
-      const double* pe = psi2 + (size_t)t * KP;
+      const double* pe = psi + (size_t)t * KP;
       double ex = 0.0;
 #pragma unroll
       for (int k = 0; k < KP; ++k) ex = fma(xr[k], pe[k], ex);
-      const double f = a * exp2(ex) * eg[2 * e + side] * inv_log2e;
+      const double f = a * exp(ex) * eg[2 * e + side];
 #pragma unroll
       for (int k = 0; k < KP; ++k) acc[k] = fma(f, pe[k], acc[k]);
     }

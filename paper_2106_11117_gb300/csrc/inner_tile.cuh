@@ -50,13 +50,15 @@ struct TileDev {
   int core_max;          // largest core
   int chunk;             // slabs per work unit
   int chunks;            // work units per tile
+  const int* xptr;       // [n_tiles + 1] each tile's range of slots beyond the fourth in xs
+  int xs_max;            // most such slots of a tile
 };
 
 // Shared-memory layout of k_inner_tile (bytes), the same on host and device.
 struct TileSmem {
-  size_t plane, node, se, sg, sw, sud, total;
+  size_t plane, node, se, sg, sw, sud, sxs, sxw, total;
 };
-__host__ __device__ inline TileSmem tile_smem_layout(int n_all_max, int comp_max, int core_max, int vec,
+__host__ __device__ inline TileSmem tile_smem_layout(int n_all_max, int comp_max, int core_max, int xs_max, int vec,
                                                      int real_bytes) {
   TileSmem L;
   const size_t row = size_t(vec) * real_bytes;  // 16 bytes
@@ -66,7 +68,9 @@ __host__ __device__ inline TileSmem tile_smem_layout(int n_all_max, int comp_max
   L.sg = L.se + size_t(comp_max) * 16;                        // n_all_max rows of g
   L.sw = L.sg + size_t(n_all_max) * row;                      // comp_max x 4 rows of weights
   L.sud = L.sw + size_t(comp_max) * 4 * row;                  // 2 buffers x core_max x (u, d)
-  L.total = L.sud + 2 * size_t(core_max) * 2 * row;
+  L.sxs = L.sud + 2 * size_t(core_max) * 2 * row;             // xs_max int2: slots beyond the fourth
+  L.sxw = (L.sxs + size_t(xs_max) * 8 + 15) / 16 * 16;        // 2 buffers x xs_max rows of their weights
+  L.total = L.sxw + 2 * size_t(xs_max) * row;
   return L;
 }
 
@@ -92,7 +96,7 @@ k_inner_tile(TileDev tp, int S, const Real* __restrict__ W, const Real* __restri
              const InnerCoef<Real> k, Real kappa) {
   static_assert(VEC * sizeof(Real) == 16, "one 16-byte row per node and slab");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const TileSmem L = tile_smem_layout(tp.n_all_max, tp.comp_max, tp.core_max, VEC, sizeof(Real));
+  const TileSmem L = tile_smem_layout(tp.n_all_max, tp.comp_max, tp.core_max, tp.xs_max, VEC, sizeof(Real));
   Real* const plane0 = reinterpret_cast<Real*>(smem_raw + L.plane);
   Real* const plane1 = plane0 + (size_t)(tp.n_all_max + 1) * VEC;
   int* const snode = reinterpret_cast<int*>(smem_raw + L.node);
@@ -100,6 +104,9 @@ k_inner_tile(TileDev tp, int S, const Real* __restrict__ W, const Real* __restri
   Real* const sg = reinterpret_cast<Real*>(smem_raw + L.sg);
   Real* const sw = reinterpret_cast<Real*>(smem_raw + L.sw);
   Real* const sud = reinterpret_cast<Real*>(smem_raw + L.sud);
+  int2* const sxs = reinterpret_cast<int2*>(smem_raw + L.sxs);
+  Real* const sxw = reinterpret_cast<Real*>(smem_raw + L.sxw);
+  __shared__ int slen[64];  // core + layers 1..k of the current tile
   const int p = PC > 0 ? PC : k.p;
   const int n_slabs = S / VEC;
   const int64_t n_units = (int64_t)tp.n_tiles * tp.chunks;
@@ -113,10 +120,13 @@ k_inner_tile(TileDev tp, int S, const Real* __restrict__ W, const Real* __restri
     const int n_comp = len[p - 2];  // nodes of the first substep
     const int n_all = len[p - 1];
     const int n_core = len[0];
+    const int x0 = tp.xptr[t], n_x = tp.xptr[t + 1] - x0;
 
     // ---- per tile: ids to shared memory, slots and 1/m to registers ---------
     for (int a = threadIdx.x; a < n_all; a += NT) snode[a] = tp.node[base + a];
     for (int a = threadIdx.x; a < n_comp; a += NT) sse[a] = tp.se[base + a];
+    for (int e = threadIdx.x; e < n_x; e += NT) sxs[e] = tp.xs[x0 + e];
+    for (int q = threadIdx.x; q < p; q += NT) slen[q] = len[q];
     int2 sj[IT];
     Real mi[IT];
     int xp[IT];
@@ -152,6 +162,8 @@ k_inner_tile(TileDev tp, int S, const Real* __restrict__ W, const Real* __restri
         cp16(ud + (size_t)a * 2 * VEC, u + is);
         cp16(ud + ((size_t)a * 2 + 1) * VEC, d + is);
       }
+      Real* xw = sxw + (size_t)b * tp.xs_max * VEC;
+      for (int e = threadIdx.x; e < n_x; e += NT) cp16(xw + (size_t)e * VEC, W + (size_t)sxs[e].y * S + s0);
       cp_commit();
     };
     prefetch(sl0, 0);
@@ -201,6 +213,7 @@ k_inner_tile(TileDev tp, int S, const Real* __restrict__ W, const Real* __restri
       __syncthreads();  // staging of g and the weights is free again
       if (sl + 1 < sl1) prefetch(sl + 1, b ^ 1);
       const Real* ud = sud + (size_t)b * tp.core_max * 2 * VEC;
+      const Real* xw = sxw + (size_t)b * tp.xs_max * VEC;
 
       // ---- substeps m = 1 .. p-1 --------------------------------------------
 #pragma unroll(PC > 0 ? PC - 1 : 1)
@@ -208,7 +221,7 @@ k_inner_tile(TileDev tp, int S, const Real* __restrict__ W, const Real* __restri
         const Real* cur = (mm & 1) ? plane0 : plane1;
         Real* nxt = (mm & 1) ? plane1 : plane0;
         const bool last = (mm == p - 1);
-        const int lm = len[p - 1 - mm];  // core and layers 1..p-1-m
+        const int lm = slen[p - 1 - mm];  // core and layers 1..p-1-m
         const Real opb = k.opb[mm], beta = k.beta[mm], cm = k.cm[mm];
 #pragma unroll
         for (int j = 0; j < IT; ++j) {
@@ -228,10 +241,10 @@ k_inner_tile(TileDev tp, int S, const Real* __restrict__ W, const Real* __restri
               for (int c = 0; c < VEC; ++c) acc[c] = couple(acc[c], w[j][q].v[c], Real(1), rj.v[c], vi[c]);
             }
             const int nx = (xp[j] >> 1) & 15;
-            for (int e = 0; e < nx; ++e) {  // slots beyond the fourth (nodes of the fans)
-              const int2 o = tp.xs[(xp[j] >> 5) + e];
-              const Pack<Real, VEC> wo = ldp<Real, VEC>(W + (size_t)o.y * S + s0);
-              const Pack<Real, VEC> rj = ldp<Real, VEC>(cur + (size_t)o.x * VEC);
+            for (int e = (xp[j] >> 5) - x0; nx > 0 && e < (xp[j] >> 5) - x0 + nx; ++e) {
+              // slots beyond the fourth (nodes of the fans), staged like the others
+              const Pack<Real, VEC> wo = ldp<Real, VEC>(xw + (size_t)e * VEC);
+              const Pack<Real, VEC> rj = ldp<Real, VEC>(cur + (size_t)sxs[e].x * VEC);
 #pragma unroll
               for (int c = 0; c < VEC; ++c) acc[c] = couple(acc[c], wo.v[c], Real(1), rj.v[c], vi[c]);
             }

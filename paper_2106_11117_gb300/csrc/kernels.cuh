@@ -128,8 +128,11 @@ __device__ __forceinline__ double ricker_scaled(const RaggedF& rf, int s) {
   return rf.amp * (1.0 - 2.0 * x) * exp(-x) * sc;
 }
 
-__device__ __forceinline__ float exp2_r(float x) { return exp2f(x); }
-__device__ __forceinline__ double exp2_r(double x) { return exp2(x); }
+// The coefficient c_e^2 = exp(xi . psi_e): the FP32 path keeps psi scaled by
+// log2(e) and calls exp2f; the FP64 path keeps psi as given and calls exp,
+// so that its c^2 carries no rounding of the scaled basis.
+__device__ __forceinline__ float coef_exp(float x) { return exp2f(x); }
+__device__ __forceinline__ double coef_exp(double x) { return exp(x); }
 
 // Arithmetic of the inner substeps with every rounding written out (no
 // contraction left to the compiler), so that the kernels that run the
@@ -184,13 +187,13 @@ __device__ __forceinline__ Lane lane_of(int SB) {
 }
 
 // ---------------------------------------------------------------------------
-// Per-sample edge weights K_ij(w) = sum_e exp2(xi . psi2[e]) G_e[i][j].
+// Per-sample edge weights K_ij(w) = sum_e exp(xi . psi[e]) G_e[i][j].
 // One thread per (edge, sample).  Once per solve.
 // ---------------------------------------------------------------------------
 template <typename Real, int KP>
 __global__ void __launch_bounds__(256)
 k_edge_weights(int64_t n_edges, int S, int SB, const int2* __restrict__ ee,
-               const Real* __restrict__ eg, const Real* __restrict__ psi2,
+               const Real* __restrict__ eg, const Real* __restrict__ psi,
                const Real* __restrict__ xi, Real* __restrict__ W, const Real* __restrict__ sig = nullptr) {
   const int ls = threadIdx.x & (SB - 1);
   const int NB = blockDim.x / SB;
@@ -207,11 +210,11 @@ k_edge_weights(int64_t n_edges, int S, int SB, const int2* __restrict__ ee,
     for (int side = 0; side < 2; ++side) {
       const int t = side ? el.y : el.x;
       if (t < 0) continue;
-      const Real* pe = psi2 + (size_t)t * KP;
+      const Real* pe = psi + (size_t)t * KP;
       Real acc = Real(0);
 #pragma unroll
       for (int k = 0; k < KP; ++k) acc = fma(xr[k], __ldg(pe + k), acc);
-      w = fma(exp2_r(acc), eg[2 * e + side], w);
+      w = fma(coef_exp(acc), eg[2 * e + side], w);
     }
     W[(size_t)e * S + s] = sig ? w * sg : w;
   }

@@ -430,7 +430,8 @@ int64_t tile_cap(const lflts_ctx* c, int var) {
 }
 template <typename Real>
 size_t tile_smem(const TileDev& td, int var) {
-  return tile_smem_layout(td.n_all_max, td.comp_max, td.core_max, tile_shape<Real>(var).vec, sizeof(Real)).total;
+  return tile_smem_layout(td.n_all_max, td.comp_max, td.core_max, td.xs_max, tile_shape<Real>(var).vec, sizeof(Real))
+      .total;
 }
 constexpr size_t kTileSmemMax = 220 * 1024;
 
@@ -800,6 +801,24 @@ bool tile_ok(lflts_ctx* c, MeshGPU& mg, int n_R, int64_t S, int p, int var) {
         }
         dt.dev.comp_max = comp_max;
         dt.dev.core_max = core_max;
+        // each tile's range of slots beyond the fourth: the plan appends them
+        // tile after tile, node after node, so the ranges are consecutive
+        std::vector<int32_t> xptr(size_t(dt.dev.n_tiles) + 1, 0);
+        int xs_max = 0;
+        for (int t = 0; t < dt.dev.n_tiles; ++t) {
+          int32_t n = 0;
+          for (int32_t a = tp.ptr[t]; a < tp.ptr[t + 1]; ++a) {
+            const int32_t k = (tp.xp[a] >> 1) & 15;
+            if (k && (tp.xp[a] >> 5) != xptr[t] + n) dt.ok = false;  // not consecutive: no tiled kernel
+            n += k;
+          }
+          xptr[t + 1] = xptr[t] + n;
+          xs_max = std::max(xs_max, int(n));
+        }
+        int* d_xptr = nullptr;
+        if (upload(c, &d_xptr, xptr.data(), xptr.size())) dt.ok = false;
+        dt.dev.xptr = d_xptr;
+        dt.dev.xs_max = xs_max;
         dt.ok = true;
       }
     }
@@ -1904,7 +1923,9 @@ int lflts_mesh_add(lflts_ctx* c, const double* xy, int64_t n_nodes, const int32_
     }
     std::vector<float> eg32(eg64.begin(), eg64.end());
     std::vector<float> minv32(h.minv.begin(), h.minv.end());
-    std::vector<float> psi32(h.psi2.begin(), h.psi2.end());
+    const double log2e = 1.4426950408889634073599246810019;
+    std::vector<float> psi32(h.psi.size());  // scaled by log2(e) for exp2f
+    for (size_t k = 0; k < psi32.size(); ++k) psi32[k] = float(h.psi[k] * log2e);
     LF_TRY(upload(c, &mg->adj_ptr, h.adj_ptr.data(), h.adj_ptr.size()));
     LF_TRY(upload(c, &mg->adj, adj.data(), na));
     std::vector<int4> ell(static_cast<size_t>(h.n_free) * 2);
@@ -1929,7 +1950,7 @@ int lflts_mesh_add(lflts_ctx* c, const double* xy, int64_t n_nodes, const int32_
     LF_TRY(upload(c, &mg->minv32, minv32.data(), minv32.size()));
     LF_TRY(upload(c, &mg->minv64, h.minv.data(), h.minv.size()));
     LF_TRY(upload(c, &mg->psi32, psi32.data(), psi32.size()));
-    LF_TRY(upload(c, &mg->psi64, h.psi2.data(), h.psi2.size()));
+    LF_TRY(upload(c, &mg->psi64, h.psi.data(), h.psi.size()));
     LF_TRY(upload(c, &mg->new2old, h.new2old.data(), h.new2old.size()));
   }
   *mesh_id = static_cast<int>(c->meshes.size());

@@ -127,12 +127,11 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
   std::vector<int32_t> enew(n_tri);
   for (int64_t k = 0; k < n_tri; ++k) enew[eorder[k]] = static_cast<int32_t>(k);
 
-  // ---- psi scaled by log2(e), padded, in the new element order -----------
-  const double log2e = 1.4426950408889634073599246810019;
-  m.psi2.assign(static_cast<size_t>(n_tri) * m.KP, 0.0);
+  // ---- psi, padded, in the new element order -------------------------------
+  m.psi.assign(static_cast<size_t>(n_tri) * m.KP, 0.0);
   for (int64_t e = 0; e < n_tri; ++e)
     for (int k = 0; k < K; ++k)
-      m.psi2[static_cast<size_t>(enew[e]) * m.KP + k] = psi[static_cast<size_t>(e) * K + k] * log2e;
+      m.psi[static_cast<size_t>(enew[e]) * m.KP + k] = psi[static_cast<size_t>(e) * K + k];
 
   // ---- lumped mass ---------------------------------------------------------
   std::vector<double> mass(n_nodes, 0.0);

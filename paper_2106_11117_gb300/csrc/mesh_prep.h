@@ -47,7 +47,7 @@ struct HostMesh {
   std::vector<int32_t> edge_e0, edge_e1;   // element ids (new order), e1 = -1 on the boundary
   std::vector<double> edge_G0, edge_G1;    // G_e0[i][j], G_e1[i][j] (0 when e1 = -1)
   std::vector<double> minv;                // [n_free] 1 / m_i (lumped mass)
-  std::vector<double> psi2;                // [n_tri][KP] psi * log2(e), zero padded
+  std::vector<double> psi;                 // [n_tri][KP] psi, zero padded (new element order)
   std::vector<double> xy;                  // [n_nodes][2] coordinates, internal order
   std::vector<int32_t> tri;                // [n_tri][3] vertices in the caller's numbering and order
   std::vector<double> area;                // [n_tri] |T| in the caller's element order

@@ -114,3 +114,33 @@ def test_adjoint_with_point_source(lf, ctx):
     Q, G = ctx.grad(h, xi, precision=64, ckpt_every=3)
     assert rel_err(Q, Qo) <= 1e-12
     assert rel_err(G, Go) <= 1e-9, rel_err(G, Go)
+
+
+def test_fp32_adjoint_against_fd_on_the_adjoint_workload_mesh(lf, ctx):
+    """The FP32 adjoint on the mesh of the adjoint workload (256^2 base cells,
+    box refined 8x, p = 8, K = 16 field terms, 108 k free nodes) over a short
+    horizon (120 outer steps, a QoI box next to the initial pulse, so that Q
+    and its gradient are not small), against central differences of the FP64
+    solve (delta = 1e-6, all 2K perturbed draws of every draw in one batch):
+    within 1e-4 of each draw's largest |dQ/dxi_k|."""
+    from workload import CONFIG_ADJOINT as cfg, box_qoi_weights, level_problem, xi_uniform
+    lev = level_problem(cfg, 0)
+    idx, g = box_qoi_weights(lev["mesh"], (0.25, 0.4, 0.25, 0.4))
+    lev = dict(lev, n_steps=120, qoi_idx=idx, qoi_w=g)
+    S, K, delta = 4, cfg.K, 1e-6
+    xi = np.ascontiguousarray(xi_uniform(cfg.seed, 0, S, K))
+    h = ctx.add_level(lev)
+    Q32, G32 = ctx.grad(h, xi, precision=32, ckpt_every=16)
+    pert = np.repeat(xi, 2 * K, axis=0).reshape(S, 2 * K, K)
+    for k in range(K):
+        pert[:, 2 * k, k] += delta
+        pert[:, 2 * k + 1, k] -= delta
+    Qp = ctx.solve(h, np.ascontiguousarray(pert.reshape(S * 2 * K, K)), precision=64).reshape(S, K, 2)
+    fd = (Qp[:, :, 0] - Qp[:, :, 1]) / (2 * delta)
+    Q64 = ctx.solve(h, xi, precision=64)
+    assert np.abs(Q64).max() > 1e-2
+    assert np.abs(Q32 - Q64).max() <= 1e-5 * np.abs(Q64).max()
+    for s in range(S):
+        scale = np.abs(fd[s]).max()
+        assert scale > 0
+        assert np.abs(G32[s] - fd[s]).max() <= 1e-4 * scale, (s, np.abs(G32[s] - fd[s]).max() / scale)
