@@ -201,12 +201,14 @@ def slice_steps(N, n_slices):
     return [N * (k + 1) // n_slices - N * k // n_slices for k in range(n_slices)]
 
 
-def setup_gpu(cfg, rank, n_slices):
+def setup_gpu(cfg, rank, n_slices, autotune=True):
     import torch
     from paper_2106_11117_gb300 import build, lflts
     from workload import level_problem, xi_uniform
     build.build()
     ctx = lflts.Context(torch.cuda.current_device())
+    if not autotune:  # the default launch shapes (for a launch list under a profiler)
+        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_AUTOTUNE, 0)
     hs = []
     for l in range(cfg.levels):
         lev = level_problem(cfg, l)
@@ -295,7 +297,7 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         pool = OraclePool(args.cpu_cores or os.cpu_count() or 1)
     n_sl = args.slices
-    W = setup_gpu(cfg, rank, n_sl)
+    W = setup_gpu(cfg, rank, n_sl, autotune=not args.no_autotune)
     lf = W["lflts"]
     ctx = W["ctx"]
     st = torch.cuda.current_stream()
@@ -439,6 +441,21 @@ def time_to_eps(eps=2e-3):
 # Name of the inner kernel class in the roofline record.
 INNER_NAME = "k_inner (one launch per substep) / k_inner_fused"
 
+# DRAM traffic of one captured launch per kernel class (ncu, dram__bytes_read.sum +
+# dram__bytes_write.sum, --set full, one launch of level 3 of square128-p8-K8 with
+# 32 draws: profiles/k_inner_square128-L3-S32.md, profiles/k_coarse_square128-L3-S32.md)
+# with its algorithmic bytes, and the hash of the kernel source it was taken
+# with: a changed source makes the figure stale and the record's traffic null.
+CAPTURED = {"kernels_sha16": "bba516a503aa701b",
+            "inner": {"dram_bytes": 553.7088e6 + 91.908352e6, "alg_bytes": 16.0 * 805987 * 32},
+            "coarse": {"dram_bytes": 925.46048e6 + 334.082304e6, "alg_bytes": 12.0 * 1838369 * 32}}
+
+
+def _kernels_sha16():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2106_11117_gb300", "csrc", "kernels.cuh"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
 
 def _timed_passes(lf, ctx, step, st, warmup, steps, profile_steps=1, local=0):
     """W warm-up steps, K timed steps (CUDA events on `st`, no per-launch
@@ -477,17 +494,24 @@ def _roofline(prof, classes, names):
     achieved = algorithmic bytes / time over its launches (the library books
     3 values per free node and coarse launch, 4 per node of R and inner
     substep, 3 per node of R for a launch of all substeps; per-draw edge
-    weights not counted), against the measured HBM copy bandwidth.  traffic
-    (DRAM bytes per launch from ncu) is null here: the figures in profiles/
-    belong to captures of single launches, named there."""
+    weights not counted), against the measured HBM copy bandwidth.  traffic:
+    DRAM bytes per launch, the captured launch's DRAM/algorithmic ratio times
+    this class's algorithmic bytes per launch (traffic grows with the draws
+    and nodes a launch covers), null without a capture of the current kernel
+    source."""
     peak, peak_kind = _peaks()
     total = sum(v["ms"] for v in prof.values()) or 1.0
     dom = max(classes, key=lambda k: prof[k]["ms"])
     pd = prof[dom]
     achieved = pd["alg_bytes"] / (pd["ms"] * 1e-3) / 1e9 if pd["ms"] > 0 else 0.0
     per = pd["alg_bytes"] / max(pd["launches"], 1)
+    cap = CAPTURED.get(dom)
+    traffic = None
+    if cap and CAPTURED["kernels_sha16"] == _kernels_sha16():
+        traffic = cap["dram_bytes"] / cap["alg_bytes"] * per
     return {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
-            "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "traffic_over_alg": traffic / per if traffic else None,
             "alg_bytes_per_launch": per, "launches": pd["launches"],
             "avg_launch_ms": pd["ms"] / max(pd["launches"], 1),
             "share_of_kernel_time": round(pd["ms"] / total, 4)}
@@ -833,6 +857,11 @@ def run_profile_case(args):
     if args.profile_samples:
         S = args.profile_samples
     ctx = lflts.Context(0)
+    if args.no_autotune:
+        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_AUTOTUNE, 0)
+    if args.inner != "auto":  # one launch per substep, or the tiled kernel, forced
+        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_FUSED_INNER, 0)
+        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_TILED_INNER, 2 if args.inner == "tiled" else 0)
     h = ctx.add_level(level_problem(cfg, l))
     xi = torch.from_numpy(xi_uniform(cfg.seed, l, S, cfg.K)).cuda()
     Q = torch.zeros(S, dtype=torch.float64, device="cuda")
@@ -862,6 +891,8 @@ def main():
     ap.add_argument("--tte-skip-plain", action="store_true")
     ap.add_argument("--tte-skip-bw", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default launch shapes (the autotuner's timings are not valid under a profiler)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cores", type=int, default=0)
     ap.add_argument("--cpu-rounds", type=int, default=8,
@@ -872,6 +903,8 @@ def main():
                     help="run only a few steps of one mesh solve (for ncu captures)")
     ap.add_argument("--profile-steps", type=int, default=4)
     ap.add_argument("--profile-samples", type=int, default=0)
+    ap.add_argument("--inner", choices=["auto", "substep", "tiled"], default="auto",
+                    help="inner-substep kernel of a --profile-case run")
     ap.add_argument("--lts-vs-lf", action="store_true", help="compare LF-LTS with standard leapfrog")
     ap.add_argument("--lts-vs-lf-levels", type=int, default=2)
     args = ap.parse_args()

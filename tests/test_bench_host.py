@@ -56,3 +56,21 @@ def test_slices_cover_every_outer_step_once():
             st = bench.slice_steps(N, n)
             assert sum(st) == N and len(st) == n
             assert max(st) - min(st) <= 1
+
+
+def test_roofline_traffic_from_the_capture_of_the_current_kernels():
+    """traffic = captured DRAM/algorithmic ratio x algorithmic bytes per
+    launch while the kernel source is the captured one; null otherwise."""
+    prof = {"coarse": {"launches": 10, "ms": 20.0, "alg_bytes": 100e9},
+            "inner": {"launches": 70, "ms": 60.0, "alg_bytes": 360e9}}
+    names = {"coarse": "k_coarse", "inner": "k_inner"}
+    r = bench._roofline(prof, ("coarse", "inner"), names)
+    cap = bench.CAPTURED["inner"]
+    assert abs(r["traffic"] - cap["dram_bytes"] / cap["alg_bytes"] * 360e9 / 70) < 1.0
+    assert 1.0 < r["traffic_over_alg"] < 2.0
+    saved = bench.CAPTURED["kernels_sha16"]
+    try:
+        bench.CAPTURED["kernels_sha16"] = "0" * 16
+        assert bench._roofline(prof, ("coarse", "inner"), names)["traffic"] is None
+    finally:
+        bench.CAPTURED["kernels_sha16"] = saved
