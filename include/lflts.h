@@ -87,8 +87,12 @@ enum {
                                  neighbouring tiles) with each node's state in registers and r_m in
                                  shared memory; same results bit for bit, uniform batches only:
                                  0 never; 1 (default) autotuned where |R| > 2048; 2 always */
-  LFLTS_OPT_TILE_CAP = 7      /* 0 (default): tiles as large as the kernel's registers allow; n >= 16:
+  LFLTS_OPT_TILE_CAP = 7,     /* 0 (default): tiles as large as the kernel's registers allow; n >= 16:
                                  at most n computed nodes per tile (more, smaller tiles) */
+  LFLTS_OPT_GRAPH_CACHE = 8   /* instantiated solve graphs kept per workspace (default 8, >= 1); a
+                                 new graph beyond it first synchronises the stream and destroys the
+                                 least recently used ones (an adaptive MLMC run changes its batch
+                                 sizes every iteration) */
 };
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -417,11 +421,14 @@ int lflts_profile_reset(lflts_ctx* ctx);
 int lflts_profile_read(lflts_ctx* ctx, int kernel_class, int64_t* launches,
                        double* ms, double* alg_bytes);
 int lflts_launch_count(lflts_ctx* ctx, int64_t* launches);
+/* Instantiated solve graphs the context holds (all workspaces), for the
+ * bound LFLTS_OPT_GRAPH_CACHE sets.  Errors: LFLTS_ERR_ARG for NULL pointers. */
+int lflts_graph_cache_size(lflts_ctx* ctx, int64_t* n);
 
 /* Set an LFLTS_OPT_* option of the context.
  * Errors: LFLTS_ERR_ARG for a NULL context, an unknown option, a fused-inner mode
- * outside {0, 1, 2}, a tiled-inner mode outside {0, 1, 2} or a tile capacity
- * in [1, 15] or negative. */
+ * outside {0, 1, 2}, a tiled-inner mode outside {0, 1, 2}, a tile capacity
+ * in [1, 15] or negative, or a graph cache below 1. */
 int lflts_set_option(lflts_ctx* ctx, int option, int64_t value);
 
 /*

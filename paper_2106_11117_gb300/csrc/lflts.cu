@@ -174,6 +174,7 @@ struct lflts_ctx {
   int64_t tune_launches = 0;
   int64_t graph_launches = 0;
   bool graphs = true;
+  int64_t graph_cap = 8;  // instantiated solve graphs kept per workspace (least recently used dropped)
   bool autotune = true;
   int fused_mode = 1;            // fused inner kernel: 0 never, 1 autotuned, 2 always where it fits
   int tile_mode = 1;             // tiled inner kernel: 0 never, 1 autotuned, 2 always where it fits
@@ -1180,13 +1181,25 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   key.ragged = rg ? rg->hash : 0;
   key.dts = rg ? rg->d_dts : nullptr;
   key.sig = rg ? rg->d_sig : nullptr;
-  for (auto& ge : ws.graphs)
-    if (ge.key == key) {
+  for (size_t k = 0; k < ws.graphs.size(); ++k)
+    if (ws.graphs[k].key == key) {
+      // most recently used last: eviction takes the front
+      std::rotate(ws.graphs.begin() + k, ws.graphs.begin() + k + 1, ws.graphs.end());
+      const GraphEntry& ge = ws.graphs.back();
       LF_CUDA(c, cudaGraphLaunch(ge.exec, st));
       c->launches += ge.kernels;
       c->graph_launches++;
       return 0;
     }
+  // a full cache gives up its least recently used graphs first (after the
+  // stream has finished with them; outside any capture)
+  if (!ws.graphs.empty() && int64_t(ws.graphs.size()) >= c->graph_cap) {
+    LF_CUDA(c, cudaStreamSynchronize(st));
+    while (!ws.graphs.empty() && int64_t(ws.graphs.size()) >= c->graph_cap) {
+      cudaGraphExecDestroy(ws.graphs.front().exec);
+      ws.graphs.erase(ws.graphs.begin());
+    }
+  }
   const int64_t l0 = c->launches;
   LF_CUDA(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   const int rc = body();
@@ -2382,6 +2395,10 @@ int lflts_set_option(lflts_ctx* c, int option, int64_t value) {
       c->fused_mode = static_cast<int>(value);
       for (auto& m : c->meshes) m->tuned.clear();  // re-tune with the new candidate set
       return LFLTS_OK;
+    case LFLTS_OPT_GRAPH_CACHE:
+      if (value < 1) return fail(c, LFLTS_ERR_ARG, "set_option: graph cache must hold at least 1 graph");
+      c->graph_cap = value;
+      return LFLTS_OK;
     case LFLTS_OPT_TILED_INNER:
       if (value < 0 || value > 2) return fail(c, LFLTS_ERR_ARG, "set_option: tiled inner mode must be 0, 1 or 2");
       c->tile_mode = static_cast<int>(value);
@@ -2404,6 +2421,17 @@ int lflts_get_stats(lflts_ctx* c, int64_t out[4]) {
   out[2] = c->tune_launches;
   out[3] = 0;
   for (auto& m : c->meshes) out[3] += static_cast<int64_t>(m->tuned.size());
+  return LFLTS_OK;
+}
+
+int lflts_graph_cache_size(lflts_ctx* c, int64_t* n) {
+  if (!c || !n) return LFLTS_ERR_ARG;
+  int64_t k = 0;
+  for (auto& w : c->ws) k += static_cast<int64_t>(w->graphs.size());
+  for (auto& w : c->fws)
+    if (w) k += static_cast<int64_t>(w->graphs.size());
+  if (c->gws) k += static_cast<int64_t>(c->gws->graphs.size());
+  *n = k;
   return LFLTS_OK;
 }
 

@@ -39,13 +39,14 @@ EXPORTED = [
     "lflts_profile_enable", "lflts_profile_reset", "lflts_profile_read", "lflts_launch_count",
     "lflts_qoi_reduce_noalloc", "lflts_grad_xi", "lflts_set_option", "lflts_get_stats",
     "lflts_source_add", "lflts_interp_weights", "lflts_run_pairs_slice", "lflts_field_interp_add",
-    "lflts_run_field_pair",
+    "lflts_run_field_pair", "lflts_graph_cache_size",
 ]
 LFLTS_OPT_GRAPHS = 1
 LFLTS_OPT_AUTOTUNE = 2
 LFLTS_OPT_FUSED_INNER = 5
 LFLTS_OPT_TILED_INNER = 6
 LFLTS_OPT_TILE_CAP = 7
+LFLTS_OPT_GRAPH_CACHE = 8
 
 
 class LibraryNotBuilt(RuntimeError):
@@ -118,6 +119,7 @@ def load(path: str | None = None):
         "lflts_profile_reset": (i32, [vp]),
         "lflts_profile_read": (i32, [vp, i32, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "lflts_launch_count": (i32, [vp, C.POINTER(i64)]),
+        "lflts_graph_cache_size": (i32, [vp, C.POINTER(i64)]),
         "lflts_qoi_reduce_noalloc": (i32, [vp, vp, i32, i64, i64, vp, vp, i64, vp, vp]),
         "lflts_grad_xi": (i32, [vp, C.POINTER(SolveDesc), vp, i64, i32, vp, vp, i32, vp]),
         "lflts_set_option": (i32, [vp, i32, i64]),
@@ -320,6 +322,12 @@ def lflts_get_stats(ctx):
     _check(ctx, load().lflts_get_stats(ctx, _ptr(out)))
     return {"launches": int(out[0]), "graph_launches": int(out[1]), "tune_launches": int(out[2]),
             "tuned_shapes": int(out[3])}
+
+
+def lflts_graph_cache_size(ctx):
+    n = C.c_int64()
+    _check(ctx, load().lflts_graph_cache_size(ctx, C.byref(n)))
+    return n.value
 
 
 def lflts_launch_count(ctx):

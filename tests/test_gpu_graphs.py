@@ -165,3 +165,44 @@ def test_long_solves_launch_without_graph(lf):
             assert torch.isfinite(q).all()
     finally:
         ctx.close()
+
+
+def test_graph_cache_is_bounded(lf):
+    """Solves with ever new batch sizes (as an adaptive Alg. 1 issues them)
+    keep at most LFLTS_OPT_GRAPH_CACHE graphs per workspace: the least
+    recently used are destroyed, a graph still held is replayed, and every
+    result equals the run without graphs bit for bit."""
+    import torch
+    lev = small_level(n=12, p=3, K=4)
+    st = torch.cuda.Stream()
+    outs = {}
+    for graphs in (0, 1):
+        ctx = lf.Context(0)
+        try:
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_AUTOTUNE, 0)
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_GRAPHS, graphs)
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_GRAPH_CACHE, 2)
+            h = ctx.add_level(lev)
+            d = h.desc(32)
+            res = []
+            for S in (8, 12, 16, 20, 16, 24, 8):
+                xi = torch.from_numpy(draws(S, 4, seed=S)).cuda()
+                Q = torch.zeros(S, dtype=torch.float64, device="cuda")
+                lf.lflts_solve(ctx.h, d, xi, S, Q, None, lf.LFLTS_MEM_DEVICE, st.cuda_stream)
+                st.synchronize()
+                res.append(Q.cpu().numpy())
+                assert lf.lflts_graph_cache_size(ctx.h) <= 2
+            if graphs:
+                assert lf.lflts_graph_cache_size(ctx.h) == 2
+                assert lf.lflts_get_stats(ctx.h)["graph_launches"] == 7
+            outs[graphs] = res
+        finally:
+            ctx.close()
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+    with pytest.raises(lf.LfltsError):
+        c2 = lf.Context(0)
+        try:
+            lf.lflts_set_option(c2.h, lf.LFLTS_OPT_GRAPH_CACHE, 0)
+        finally:
+            c2.close()
