@@ -447,8 +447,8 @@ INNER_NAME = "k_inner (one launch per substep) / k_inner_fused"
 # with its algorithmic bytes, and the hash of the kernel source it was taken
 # with: a changed source makes the figure stale and the record's traffic null.
 CAPTURED = {"kernels_sha16": "bba516a503aa701b",
-            "inner": {"dram_bytes": 553.7088e6 + 91.908352e6, "alg_bytes": 16.0 * 805987 * 32},
-            "coarse": {"dram_bytes": 925.46048e6 + 334.082304e6, "alg_bytes": 12.0 * 1838369 * 32}}
+            "inner": {"dram_bytes": 553.56032e6 + 90.601728e6, "alg_bytes": 16.0 * 805987 * 32},
+            "coarse": {"dram_bytes": 925.441024e6 + 336.92416e6, "alg_bytes": 12.0 * 1838369 * 32}}
 
 
 def _kernels_sha16():
