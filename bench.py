@@ -364,8 +364,9 @@ def run_ours(args):
     SliceRunner(lf, ctx, W["jobs_d"], n_sl, lf.LFLTS_MEM_DEVICE, st.cuda_stream, W["units_slice"]).step()
     torch.cuda.synchronize()
     lf.lflts_profile_enable(ctx.h, False)
-    prof = {k: lf.lflts_profile_read(ctx.h, k) for k in ("init", "coarse", "inner", "qoi", "sums")}
-    roof = _roofline(prof, ("coarse", "inner"), {"coarse": "k_coarse", "inner": INNER_NAME})
+    prof = {k: lf.lflts_profile_read(ctx.h, k) for k in ("init", "coarse", "inner", "inner_pair", "qoi", "sums")}
+    roof = _roofline(prof, ("coarse", "inner", "inner_pair"),
+                     {"coarse": "k_coarse", "inner": INNER_NAME, "inner_pair": PAIR_NAME})
 
     tte = None
     if world == 1 and not args.no_time_to_eps:
@@ -438,23 +439,35 @@ def time_to_eps(eps=2e-3):
         ctx.close()
 
 
-# Name of the inner kernel class in the roofline record.
+# Names of the inner kernel classes in the roofline record.
 INNER_NAME = "k_inner (one launch per substep) / k_inner_fused"
+PAIR_NAME = "k_inner_pair (two substeps per launch)"
 
 # DRAM traffic of one captured launch per kernel class (ncu, dram__bytes_read.sum +
 # dram__bytes_write.sum, --set full, one launch of level 3 of square128-p8-K8 with
-# 32 draws: profiles/k_inner_square128-L3-S32.md, profiles/k_coarse_square128-L3-S32.md)
-# with its algorithmic bytes, and the hash of the kernel source it was taken
+# 32 draws: profiles/k_inner_square128-L3-S32.md, profiles/k_coarse_square128-L3-S32.md,
+# profiles/k_inner_pair_square128-L3-S32.md)
+# with its algorithmic bytes, and the hash of the kernel sources it was taken
 # with: a changed source makes the figure stale and the record's traffic null.
-CAPTURED = {"kernels_sha16": "bba516a503aa701b",
-            "inner": {"dram_bytes": 553.56032e6 + 90.601728e6, "alg_bytes": 16.0 * 805987 * 32},
-            "coarse": {"dram_bytes": 925.441024e6 + 336.92416e6, "alg_bytes": 12.0 * 1838369 * 32}}
+CAPTURED = {
+    "inner": {"src": ["kernels.cuh"], "sha16": "bba516a503aa701b",
+              "dram_bytes": 553.56032e6 + 90.601728e6, "alg_bytes": 16.0 * 805987 * 32},
+    "coarse": {"src": ["kernels.cuh"], "sha16": "bba516a503aa701b",
+               "dram_bytes": 925.441024e6 + 336.92416e6, "alg_bytes": 12.0 * 1838369 * 32},
+    # the second pair launch of a step (profiles/k_inner_pair_square128-L3-S32.md)
+    "inner_pair": {"src": ["kernels.cuh", "inner_pair.cuh"], "sha16": "810366b4ede4d2f1",
+                   "dram_bytes": 610.674688e6 + 185.878784e6, "alg_bytes": 20.0 * 805987 * 32},
+}
 
 
-def _kernels_sha16():
+def _src_sha16(src):
+    """First 16 hex digits of the SHA-256 of the named kernel sources, concatenated."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2106_11117_gb300", "csrc", "kernels.cuh"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in src:
+        with open(os.path.join(ROOT, "paper_2106_11117_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _timed_passes(lf, ctx, step, st, warmup, steps, profile_steps=1, local=0):
@@ -507,7 +520,7 @@ def _roofline(prof, classes, names):
     per = pd["alg_bytes"] / max(pd["launches"], 1)
     cap = CAPTURED.get(dom)
     traffic = None
-    if cap and CAPTURED["kernels_sha16"] == _kernels_sha16():
+    if cap and cap["sha16"] == _src_sha16(cap["src"]):
         traffic = cap["dram_bytes"] / cap["alg_bytes"] * per
     return {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -859,9 +872,12 @@ def run_profile_case(args):
     ctx = lflts.Context(0)
     if args.no_autotune:
         lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_AUTOTUNE, 0)
-    if args.inner != "auto":  # one launch per substep, or the tiled kernel, forced
+    if args.inner != "auto":  # one launch per substep, the tiled kernel or paired substeps, forced
         lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_FUSED_INNER, 0)
         lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_TILED_INNER, 2 if args.inner == "tiled" else 0)
+        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_PAIRED_INNER, 2 if args.inner == "paired" else 0)
+    if args.pair_block:
+        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_PAIR_BLOCK, args.pair_block)
     h = ctx.add_level(level_problem(cfg, l))
     xi = torch.from_numpy(xi_uniform(cfg.seed, l, S, cfg.K)).cuda()
     Q = torch.zeros(S, dtype=torch.float64, device="cuda")
@@ -903,8 +919,10 @@ def main():
                     help="run only a few steps of one mesh solve (for ncu captures)")
     ap.add_argument("--profile-steps", type=int, default=4)
     ap.add_argument("--profile-samples", type=int, default=0)
-    ap.add_argument("--inner", choices=["auto", "substep", "tiled"], default="auto",
+    ap.add_argument("--inner", choices=["auto", "substep", "tiled", "paired"], default="auto",
                     help="inner-substep kernel of a --profile-case run")
+    ap.add_argument("--pair-block", type=int, default=0,
+                    help="nodes of R per block of the paired substeps (--profile-case)")
     ap.add_argument("--lts-vs-lf", action="store_true", help="compare LF-LTS with standard leapfrog")
     ap.add_argument("--lts-vs-lf-levels", type=int, default=2)
     args = ap.parse_args()

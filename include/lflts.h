@@ -67,7 +67,8 @@ enum {
                                  adjoint inner recursion rho_{p-1}..rho_1                 */
   LFLTS_KERNEL_ADJ_EDGES = 6, /* lflts_grad_xi: per-edge FP64 accumulation of the gradient    */
   LFLTS_KERNEL_GRAD = 7,      /* lflts_grad_xi: adjoint seed and the contraction with dK/dxi */
-  LFLTS_KERNEL_CLASSES = 8
+  LFLTS_KERNEL_INNER_PAIR = 8, /* two inner LTS substeps on R in one launch (Alg. 2 loop)   */
+  LFLTS_KERNEL_CLASSES = 9
 };
 
 /* Options for lflts_set_option. */
@@ -89,10 +90,20 @@ enum {
                                  0 never; 1 (default) autotuned where |R| > 2048; 2 always */
   LFLTS_OPT_TILE_CAP = 7,     /* 0 (default): tiles as large as the kernel's registers allow; n >= 16:
                                  at most n computed nodes per tile (more, smaller tiles) */
-  LFLTS_OPT_GRAPH_CACHE = 8   /* instantiated solve graphs kept per workspace (default 8, >= 1); a
+  LFLTS_OPT_GRAPH_CACHE = 8,  /* instantiated solve graphs kept per workspace (default 8, >= 1); a
                                  new graph beyond it first synchronises the stream and destroys the
                                  least recently used ones (an adaptive MLMC run changes its batch
                                  sizes every iteration) */
+  LFLTS_OPT_PAIRED_INNER = 9, /* inner substeps two by two in one launch for a large R: blocks of R
+                                 (square cells plus a halo of their P neighbours) with r_{m+1}
+                                 exchanged in shared memory; same results bit for bit, uniform
+                                 batches only; with an odd number of substeps the first runs alone:
+                                 0 never; 1 (default) autotuned where |R| > 2048 (4 draws per thread
+                                 in FP32, 2 in FP64); always where the blocks fit in shared memory
+                                 with 2: 4 draws per thread in FP32, 2 in FP64; 3: 2; 4: 1 */
+  LFLTS_OPT_PAIR_BLOCK = 10   /* about this many nodes of R per block of the paired substeps,
+                                 16..4096 (default 144); blocks whose rows do not fit in the shared
+                                 memory of a CTA make the batch run one launch per substep */
 };
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -410,8 +421,10 @@ int lflts_qoi_reduce_noalloc(lflts_ctx* ctx, const void* u, int precision, int64
  * node and draw (4 bytes each in FP32, 8 in FP64), counted as 3 values per
  * free node for a coarse launch (u_n and u_{n-1} read, u_{n+1} written), 4
  * per node of R for one inner substep (r_m, r_{m-1} and g read, r_{m+1}
- * written) and 3 per node of R for a launch that runs all substeps of a step
- * on chip; per-draw edge weights and index data are not counted (the
+ * written), 5 per node of R for a launch of two substeps (r_m, r_{m-1}, g
+ * read, r_{m+1}, r_{m+2} written; 7 for the pair that ends the step, which
+ * reads u and d and writes d and u instead of r_{m+1}, r_{m+2}) and 3 per
+ * node of R for a launch that runs all substeps of a step on chip; per-draw edge weights and index data are not counted (the
  * coefficient can be recomputed from xi).  Reset clears the
  * counters.  lflts_launch_count returns all kernel launches of the context
  * since creation, whether profiling is on or not.
@@ -428,7 +441,8 @@ int lflts_graph_cache_size(lflts_ctx* ctx, int64_t* n);
 /* Set an LFLTS_OPT_* option of the context.
  * Errors: LFLTS_ERR_ARG for a NULL context, an unknown option, a fused-inner mode
  * outside {0, 1, 2}, a tiled-inner mode outside {0, 1, 2}, a tile capacity
- * in [1, 15] or negative, or a graph cache below 1. */
+ * in [1, 15] or negative, a graph cache below 1, a paired-inner mode outside
+ * 0..4 or a paired-substep block outside [16, 4096]. */
 int lflts_set_option(lflts_ctx* ctx, int option, int64_t value);
 
 /*

@@ -24,6 +24,7 @@
 #include "../../include/lflts.h"
 #include "adjoint.cuh"
 #include "field_qoi.cuh"
+#include "inner_pair.cuh"
 #include "inner_tile.cuh"
 #include "kernels.cuh"
 #include "mesh_prep.h"
@@ -69,6 +70,12 @@ struct MeshGPU {
     bool ok = false;
   };
   std::map<std::pair<int, int64_t>, DevTiles> tiles;
+  // block plans of the paired inner substeps per block size, uploaded
+  struct DevPairs {
+    PairDev dev{};
+    bool ok = false;
+  };
+  std::map<int, DevPairs> pairs;
 };
 
 struct Field {
@@ -112,7 +119,7 @@ struct GraphKey {
   int mesh, qoi, u0, v0, precision, p;
   double nu, dt;
   int64_t n_steps, S;
-  const void *xi, *Q, *uN, *ua, *ub, *d, *g, *r0, *r1, *r2, *W, *xipad, *qps, *qpc;
+  const void *xi, *Q, *uN, *ua, *ub, *d, *g, *r0, *r1, *r2, *r3, *W, *xipad, *qps, *qpc;
   int vec, cps, source;
   double f0, t0, famp;
   uint64_t ragged;           // segment list of a ragged batch (0: uniform)
@@ -127,7 +134,7 @@ struct GraphEntry {
 };
 
 struct Workspace {
-  Buf ua, ub, d, g, r0, r1, r2, W, xipad, xraw, qps, qpc, Q, uN;
+  Buf ua, ub, d, g, r0, r1, r2, r3, W, xipad, xraw, qps, qpc, Q, uN;
   Buf dts, sig;                        // per-draw dt and (dt / dt_ref)^2 of a ragged batch
   std::vector<double> h_dts;           // host copies of the two (kept for the async copies)
   std::vector<unsigned char> h_sig;
@@ -179,6 +186,8 @@ struct lflts_ctx {
   int fused_mode = 1;            // fused inner kernel: 0 never, 1 autotuned, 2 always where it fits
   int tile_mode = 1;             // tiled inner kernel: 0 never, 1 autotuned, 2 always where it fits
   int64_t tile_cap = 0;          // > 0: at most this many computed nodes per tile
+  int pair_mode = 1;             // paired inner substeps: 0 never, 1 autotuned, 2 always where they fit
+  int pair_block = 144;          // about this many nodes of R per block of the paired substeps
   std::vector<void*> owned;  // device allocations of meshes, fields, QoIs
   std::unique_ptr<PairRun> run;  // lflts_run_pairs_slice: the run in progress, if any
   std::vector<Interp> interps;   // lflts_field_interp_add
@@ -471,6 +480,38 @@ cudaError_t tile_call(int var, int p, bool attr_only, int smem_attr, int grid, s
   return e;
 }
 
+// Paired inner substeps: the shared memory of a CTA (rows of r_{m+1} for a
+// slab of 32 draws and the staged index data).
+template <typename Real>
+size_t pair_smem(const PairDev& pd, int vec) {
+  const int SL = (32 / vec) * vec;
+  return pair_smem_layout(pd.rows_max, pd.core_max, SL, sizeof(Real)).total;
+}
+
+// Draws per thread of the paired substeps for a shape kind (5, 6, 7: 4, 2, 1
+// draws; FP64 takes 2 or 1), 0 for other kinds.  Their slab is always 32
+// draws, so the shared memory does not depend on it.
+template <typename Real>
+int pair_vec_of_kind(int kind) {
+  if (kind == 5) return sizeof(Real) == 4 ? 4 : 0;
+  if (kind == 6) return 2;
+  if (kind == 7) return 1;
+  return 0;
+}
+
+template <typename Real, int PV>
+void launch_pair(bool last2, dim3 grid, size_t smem, cudaStream_t st, const MeshDev<Real>& md, const PairDev& pd,
+                 int S, const Real* W, const Real* cur, Real s_cur, const Real* prev, Real s_prev, const Real* g,
+                 Real* o1, Real* o2, const Real* uc, Real* un, Real* d, Real a1, Real b1, Real c1, Real a2, Real b2,
+                 Real c2, Real kappa) {
+  if (last2)
+    k_inner_pair<Real, PV, true><<<grid, 256, smem, st>>>(md, pd, S, 32 / PV, W, cur, s_cur, prev, s_prev, g, o1,
+                                                          o2, uc, un, d, a1, b1, c1, a2, b2, c2, kappa);
+  else
+    k_inner_pair<Real, PV, false><<<grid, 256, smem, st>>>(md, pd, S, 32 / PV, W, cur, s_cur, prev, s_prev, g, o1,
+                                                           o2, uc, un, d, a1, b1, c1, a2, b2, c2, kappa);
+}
+
 // One step of Alg. 2 for one batch (see kernels.cuh for the u-form): the
 // coarse launch over the free nodes, then p-1 inner launches over R (or one
 // fused launch for a small R).
@@ -486,13 +527,16 @@ struct Stepper {
   double Srb = 0, coarse_bytes = 0;
   const Real* W = nullptr;
   Real* g = nullptr;
-  Real* rbuf[3] = {nullptr, nullptr, nullptr};
+  Real* rbuf[4] = {nullptr, nullptr, nullptr, nullptr};
   bool minb6 = false;
   int cps = 16;
   bool fused = false;  // all inner substeps in one launch (R in shared memory)
   int fSB = 1;
   size_t fsmem = 0;
   int fgrid = 1;
+  int pvec = 0;  // inner substeps two by two (k_inner_pair) with pvec draws per thread, or 0
+  PairDev pdev{};
+  size_t psmem = 0;
   int tvar = -1;       // tiled inner kernel shape (-1: not tiled)
   TileDev tdev{};
   size_t tsmem = 0;
@@ -512,10 +556,12 @@ struct Stepper {
   }
 
   Stepper(lflts_ctx* c_, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R_, int64_t S_, const Real* W_,
-          Real* g_, Real* r0, Real* r1, Real* r2, int shape = 16)
+          Real* g_, Real* r0, Real* r1, Real* r2, int shape = 16, Real* r3 = nullptr)
       : c(c_), p(ds.p), n_R(n_R_), S(S_), W(W_), g(g_), S_act(S_), mgp(&mg) {
     // shape = CTAs per SM target, +100 for the register-capped kernels,
-    // +2000 for the fused inner kernel
+    // +2000 for the fused inner kernel, +3000 for the tiled one, +5000 for
+    // the paired substeps with 4 draws per thread (+6000: 2, +7000: 1; they
+    // need the fourth r buffer r3)
     minb6 = (shape % 1000) >= 100;
     const int cta_per_sm = shape % 100;
     cps = cta_per_sm;
@@ -530,14 +576,24 @@ struct Stepper {
     rbuf[0] = r0;
     rbuf[1] = r1;
     rbuf[2] = r2;
+    rbuf[3] = r3;
     lts_constants(p, ds.nu, ds.dt, beta, cm, delta, omega, c0, gamma);
     md = Sel<Real>::mesh(mg, n_R);
     gc = geometry_vec(c, h.n_free, S, VEC, cta_per_sm);
     gi = geometry_vec(c, std::max(n_R, 1), S, VEC, cta_per_sm);
     Srb = double(S) * sizeof(Real);
     coarse_bytes = 3.0 * Srb * double(h.n_free);
-    const int kind = shape / 1000;  // 0 per substep, 2 fused, 3.. tiled (shape kind - 3)
-    if (kind >= 3 && n_R > 0 && p > 1 && p <= 64 && S % tile_shape<Real>(kind - 3).vec == 0) {
+    const int kind = shape / 1000;  // 0 per substep, 2 fused, 3.. tiled (shape kind - 3), 5..7 paired
+    const int pv = pair_vec_of_kind<Real>(kind);
+    if (pv > 0 && n_R > 0 && p > 2 && r3 && S % pv == 0) {
+      auto it = mg.pairs.find(c->pair_block);
+      if (it != mg.pairs.end() && it->second.ok) {
+        pvec = pv;
+        pdev = it->second.dev;
+        psmem = pair_smem<Real>(pdev, pv);
+      }
+    }
+    if (kind >= 3 && kind - 3 < tile_shapes<Real>() && n_R > 0 && p > 1 && p <= 64 && S % tile_shape<Real>(kind - 3).vec == 0) {
       auto it = mg.tiles.find(std::make_pair(p, tile_cap<Real>(c, kind - 3)));
       if (it != mg.tiles.end() && it->second.ok) {
         tvar = kind - 3;
@@ -647,16 +703,57 @@ struct Stepper {
       return 0;
     }
     if (n_R > 0) {
-      // r_1 = -c0 g is read from g; r_2.. rotate through three buffers
+      // r_1 = -c0 g is read from g; r_2.. rotate through the r buffers (a
+      // launch never writes a buffer it reads)
       const Real* cur = g;
       Real s_cur = (Real)(-c0);
       const Real* prev = nullptr;
       Real s_prev = Real(0);
-      int nxt = 0;
-      for (int m = 1; m < p; ++m) {
+      auto pick = [&](const Real* x) -> Real* {
+        for (Real* r : rbuf)
+          if (r && r != cur && r != prev && r != x) return r;
+        return nullptr;
+      };
+      for (int m = 1; m < p;) {
+        // substeps m and m + 1 in one launch; with an odd number of substeps
+        // the first (which reads only g) runs alone, so that a pair ends the
+        // step
+        if (pvec > 0 && !dts && m + 1 < p && (p - m) % 2 == 0) {
+          const bool last2 = (m + 1 == p - 1);
+          Real* o1 = last2 ? nullptr : pick(nullptr);
+          Real* o2 = last2 ? nullptr : pick(o1);
+          Prof pr(c, st);
+          const dim3 grid(static_cast<unsigned>(pdev.n_blocks), static_cast<unsigned>((S + 31) / 32));
+          const Real a1 = (Real)(1.0 + beta[m]), b1 = (Real)beta[m], c1 = (Real)cm[m];
+          const Real a2 = (Real)(1.0 + beta[m + 1]), b2 = (Real)beta[m + 1], c2 = (Real)cm[m + 1];
+          if constexpr (sizeof(Real) == 4) {
+            if (pvec == 4)
+              launch_pair<Real, 4>(last2, grid, psmem, st, md, pdev, (int)S, W, cur, s_cur, prev, s_prev, g, o1, o2,
+                                   uc, un, d, a1, b1, c1, a2, b2, c2, kappa);
+          }
+          if (pvec == 2)
+            launch_pair<Real, 2>(last2, grid, psmem, st, md, pdev, (int)S, W, cur, s_cur, prev, s_prev, g, o1, o2, uc,
+                                 un, d, a1, b1, c1, a2, b2, c2, kappa);
+          else if (pvec == 1)
+            launch_pair<Real, 1>(last2, grid, psmem, st, md, pdev, (int)S, W, cur, s_cur, prev, s_prev, g, o1, o2, uc,
+                                 un, d, a1, b1, c1, a2, b2, c2, kappa);
+          LF_CUDA(c, cudaGetLastError());
+          // per R node r_m, r_{m-1}, g read and r_{m+1}, r_{m+2} written (the
+          // pair that ends the step: u, d read and d, u written instead of
+          // r_{m+1}, r_{m+2})
+          pr.end(LFLTS_KERNEL_INNER_PAIR, (last2 ? 7.0 : 5.0) * n_R * Srb);
+          if (!last2) {
+            prev = o1;
+            s_prev = Real(1);
+            cur = o2;
+            s_cur = Real(1);
+          }
+          m += 2;
+          continue;
+        }
         const bool last = (m == p - 1);
         const Real opb = (Real)(1.0 + beta[m]), bt = (Real)beta[m], cmm = (Real)cm[m];
-        Real* rn = rbuf[nxt];
+        Real* rn = pick(nullptr);
         Prof pr(c, st);
 #define LF_INNER(L, B, RG)                                                                                     \
   k_inner<Real, VEC, L, B, RG><<<gi.grid, 256, 0, st>>>(md, (int)S, gi.SB, W, cur, s_cur, prev, s_prev, rn, \
@@ -679,7 +776,7 @@ struct Stepper {
         s_prev = s_cur;
         cur = rn;
         s_cur = Real(1);
-        nxt = (nxt + 1) % 3;
+        ++m;
       }
     }
     return 0;
@@ -694,7 +791,7 @@ int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n
               const double* dts = nullptr) {
   Stepper<Real, VEC> stp(c, ds, mg, n_R, S, static_cast<const Real*>(ws.W.p), static_cast<Real*>(ws.g.p),
                          static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p),
-                         cta_per_sm);
+                         cta_per_sm, static_cast<Real*>(ws.r3.p));
   stp.dts = dts;  // a ragged batch: its kernels (all draws active)
   Real* uc = static_cast<Real*>(ws.ua.p);
   Real* un = static_cast<Real*>(ws.ub.p);
@@ -883,7 +980,8 @@ struct SlicedLoop : SliceTask {
              cudaStream_t st_, int cps, const RaggedSpec* rg, LoopOut<Real> o)
       : c(c_),
         stp(c_, ds, mg, n_R, S, static_cast<const Real*>(ws.W.p), static_cast<Real*>(ws.g.p),
-            static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p), cps),
+            static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p), cps,
+            static_cast<Real*>(ws.r3.p)),
         uc(static_cast<Real*>(ws.ua.p)),
         un(static_cast<Real*>(ws.ub.p)),
         d(static_cast<Real*>(ws.d.p)),
@@ -943,6 +1041,54 @@ std::unique_ptr<SliceTask> make_sliced(lflts_ctx* c, const lflts_solve_desc& ds,
 // for the fused inner kernel.  With autotuning on, the first solve of a (mesh, S, precision, p)
 // times every candidate over a few steps on the real buffers (the state is
 // re-initialised afterwards) and keeps the fastest.
+// Whether the paired inner substeps can run this batch: builds and uploads
+// the mesh's block plan once and raises the kernels' dynamic shared-memory
+// limit (outside any graph capture).
+template <typename Real>
+bool pair_ok(lflts_ctx* c, MeshGPU& mg, int n_R, int64_t S, int p) {
+  if (n_R < 1 || p < 3 || p > 64 || S < 1) return false;
+  auto it = mg.pairs.find(c->pair_block);
+  if (it == mg.pairs.end()) {
+    MeshGPU::DevPairs dp;
+    PairPlan pl;
+    if (build_pair_plan(mg.h, c->pair_block, pl) && pl.n_blocks <= INT32_MAX) {
+      int* d_rptr = nullptr;
+      int* d_ncore = nullptr;
+      int* d_row = nullptr;
+      int16_t* d_lidx = nullptr;
+      const bool up = !upload(c, &d_rptr, pl.rptr.data(), pl.rptr.size()) &&
+                      !upload(c, &d_ncore, pl.ncore.data(), pl.ncore.size()) &&
+                      !upload(c, &d_row, pl.row.data(), pl.row.size()) &&
+                      !upload(c, &d_lidx, pl.lidx.data(), pl.lidx.size());
+      if (up) {
+        dp.dev.n_blocks = static_cast<int>(pl.n_blocks);
+        dp.dev.rows_max = static_cast<int>(pl.rows_max);
+        dp.dev.core_max = static_cast<int>(pl.core_max);
+        dp.dev.rptr = d_rptr;
+        dp.dev.ncore = d_ncore;
+        dp.dev.row = d_row;
+        dp.dev.lidx = reinterpret_cast<const short*>(d_lidx);
+        dp.ok = true;
+      }
+    }
+    it = mg.pairs.emplace(c->pair_block, dp).first;
+  }
+  if (!it->second.ok) return false;
+  const size_t smem = pair_smem<Real>(it->second.dev, 1);  // the same for every draws-per-thread
+  if (smem > kTileSmemMax) return false;
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaSuccess;
+  if constexpr (sizeof(Real) == 4) {
+    e = cudaFuncSetAttribute(k_inner_pair<Real, 4, false>, attr, int(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inner_pair<Real, 4, true>, attr, int(smem));
+  }
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inner_pair<Real, 2, false>, attr, int(smem));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inner_pair<Real, 2, true>, attr, int(smem));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inner_pair<Real, 1, false>, attr, int(smem));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inner_pair<Real, 1, true>, attr, int(smem));
+  return e == cudaSuccess;
+}
+
 template <typename Real>
 int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
                  cudaStream_t st, int& vec, int& cps, const double* dts) {
@@ -952,6 +1098,14 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
     if (S % v == 0) vecs.push_back(v);
   vec = vecs.front();
   cps = 16;
+  if (c->pair_mode >= 2 && !dts && pair_ok<Real>(c, mg, n_R, S, ds.p)) {
+    // 2: 4 draws per thread in FP32, 2 in FP64; 3: 2; 4: 1
+    const int kind = c->pair_mode == 2 ? (sizeof(Real) == 4 ? 5 : 6) : c->pair_mode + 3;
+    if (S % pair_vec_of_kind<Real>(kind) == 0) {
+      cps = 1000 * kind + 16;
+      return 0;
+    }
+  }
   if (c->tile_mode >= 2 && !dts && tile_ok<Real>(c, mg, n_R, S, ds.p, c->tile_mode - 2)) {
     cps = 3016 + 1000 * (c->tile_mode - 2);
     return 0;
@@ -988,6 +1142,14 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
     if (c->fused_mode >= 1 && fused_ok<Real>(c, mg, n_R, S, v, ds.p)) {
       if (n_R <= 2048) shapes.clear();
       for (int k : {8, 16, 32, 108, 116, 132}) shapes.push_back(2000 + k);
+    }
+    // substeps two by two for a large R, with their own draws per thread (4
+    // in FP32, 2 in FP64: fewer were slower on every benchmark level), so
+    // timed with the first v only
+    if (c->pair_mode == 1 && !dts && n_R > 2048 && v == vecs.front() && pair_ok<Real>(c, mg, n_R, S, ds.p)) {
+      const int kind = sizeof(Real) == 4 ? 5 : 6;
+      if (S % pair_vec_of_kind<Real>(kind) == 0)
+        for (int k : {8, 16, 32, 108, 116, 132}) shapes.push_back(1000 * kind + k);
     }
     // the tiled inner kernel (all substeps on chip) for a large R; its own
     // draws per node do not depend on v, so it is timed with the first v only
@@ -1048,6 +1210,7 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   LF_TRY(ensure(c, ws.r0, r_bytes));
   LF_TRY(ensure(c, ws.r1, r_bytes));
   LF_TRY(ensure(c, ws.r2, r_bytes));
+  LF_TRY(ensure(c, ws.r3, r_bytes));
   LF_TRY(ensure(c, ws.W, size_t(std::max<int64_t>(h.n_edges, 1)) * S * rb));
   LF_TRY(ensure(c, ws.xipad, size_t(S) * KP * rb));
   LF_TRY(ensure(c, ws.qps, size_t(n_chunks) * S * sizeof(double)));
@@ -1136,7 +1299,7 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   // (more than kGraphMaxKernels kernels) launch directly: their graphs would
   // take seconds and gigabytes of host memory to build, and their kernels
   // outlast the launch cost anyway.
-  const int64_t inner_per_step = n_R == 0 ? 0 : (cps >= 2000 ? 1 : p - 1);
+  const int64_t inner_per_step = n_R == 0 ? 0 : (cps >= 5000 ? p / 2 : (cps >= 2000 ? 1 : p - 1));
   const int64_t est_kernels = ds.n_steps * (1 + inner_per_step);
   const bool use_graph =
       allow_graph && c->graphs && !c->profiling && st != nullptr && est_kernels <= kGraphMaxKernels;
@@ -1168,6 +1331,7 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   key.r0 = ws.r0.p;
   key.r1 = ws.r1.p;
   key.r2 = ws.r2.p;
+  key.r3 = ws.r3.p;
   key.W = ws.W.p;
   key.xipad = ws.xipad.p;
   key.qps = ws.qps.p;
@@ -1882,12 +2046,12 @@ int lflts_destroy(lflts_ctx* c) {
       if (w)
         for (auto& ge : w->graphs) cudaGraphExecDestroy(ge.exec);
     for (auto& w : c->ws)
-      for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->W, &w->xipad, &w->xraw, &w->qps,
+      for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->r3, &w->W, &w->xipad, &w->xraw, &w->qps,
                      &w->qpc, &w->Q, &w->uN, &w->dts, &w->sig})
         if (b->p) cudaFree(b->p);
     for (Workspace* w : {c->gws.get(), c->fws[0].get(), c->fws[1].get()})
       if (w)
-        for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->W, &w->xipad, &w->xraw, &w->qps,
+        for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->r3, &w->W, &w->xipad, &w->xraw, &w->qps,
                        &w->qpc, &w->Q, &w->uN, &w->dts, &w->sig})
           if (b->p) cudaFree(b->p);
     if (c->fb)
@@ -2394,6 +2558,17 @@ int lflts_set_option(lflts_ctx* c, int option, int64_t value) {
       if (value < 0 || value > 2) return fail(c, LFLTS_ERR_ARG, "set_option: fused inner mode must be 0, 1 or 2");
       c->fused_mode = static_cast<int>(value);
       for (auto& m : c->meshes) m->tuned.clear();  // re-tune with the new candidate set
+      return LFLTS_OK;
+    case LFLTS_OPT_PAIRED_INNER:
+      if (value < 0 || value > 4) return fail(c, LFLTS_ERR_ARG, "set_option: paired inner mode must be 0..4");
+      c->pair_mode = static_cast<int>(value);
+      for (auto& m : c->meshes) m->tuned.clear();
+      return LFLTS_OK;
+    case LFLTS_OPT_PAIR_BLOCK:
+      if (value < 16 || value > 4096)
+        return fail(c, LFLTS_ERR_ARG, "set_option: paired-substep block must be 16..4096 nodes");
+      c->pair_block = static_cast<int>(value);
+      for (auto& m : c->meshes) m->tuned.clear();
       return LFLTS_OK;
     case LFLTS_OPT_GRAPH_CACHE:
       if (value < 1) return fail(c, LFLTS_ERR_ARG, "set_option: graph cache must hold at least 1 graph");

@@ -413,6 +413,64 @@ void tile_nodes(const HostMesh& m, const std::vector<int32_t>& order, int64_t a0
 
 }  // namespace
 
+bool build_pair_plan(const HostMesh& m, int bn, PairPlan& out) {
+  out = PairPlan();
+  const int64_t nR = m.n_R, nP = m.n_P;
+  if (nR == 0 || bn < 1) return false;
+  const std::vector<int32_t> order = morton_order_R(m);
+  double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+  for (int64_t i = 0; i < nR; ++i) {
+    x0 = std::min(x0, m.xy[2 * i]);
+    x1 = std::max(x1, m.xy[2 * i]);
+    y0 = std::min(y0, m.xy[2 * i + 1]);
+    y1 = std::max(y1, m.xy[2 * i + 1]);
+  }
+  const double wx = std::max(x1 - x0, 1e-300), wy = std::max(y1 - y0, 1e-300);
+  // a cell of side L holds about (L / h)^2 nodes where R fills its box
+  const double h = std::sqrt(wx * wy / double(nR));
+  const double L = std::max(h, std::sqrt(double(bn)) * h);
+  const int64_t ncx = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(wx / L))),
+                ncy = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(wy / L)));
+  if (ncx * ncy > (int64_t(1) << 26)) return false;
+  std::vector<std::vector<int32_t>> byc(ncx * ncy);
+  for (int64_t a = 0; a < nR; ++a) {
+    const int32_t i = order[a];
+    const int64_t cx = std::min<int64_t>(ncx - 1, static_cast<int64_t>((m.xy[2 * i] - x0) / L));
+    const int64_t cy = std::min<int64_t>(ncy - 1, static_cast<int64_t>((m.xy[2 * i + 1] - y0) / L));
+    byc[cy * ncx + cx].push_back(i);
+  }
+  out.rptr.assign(1, 0);
+  out.lidx.assign(static_cast<size_t>(m.adj_ptr[nR]), int16_t(-1));
+  std::vector<int32_t> local(nR, -1);  // row of a node in the current block (reset after)
+  for (const auto& core : byc) {
+    if (core.empty()) continue;
+    const size_t r0 = out.row.size();
+    for (const int32_t i : core) {
+      local[i] = static_cast<int32_t>(out.row.size() - r0);
+      out.row.push_back(i);
+    }
+    for (const int32_t i : core)
+      for (int32_t t = m.adj_ptr[i]; t < m.adj_ptr[i + 1]; ++t) {
+        const int32_t j = m.adj_j[t];
+        if (j >= nP) continue;
+        if (local[j] < 0) {
+          local[j] = static_cast<int32_t>(out.row.size() - r0);
+          out.row.push_back(j);
+        }
+        if (local[j] > 32767) return false;
+        out.lidx[t] = static_cast<int16_t>(local[j]);
+      }
+    for (size_t k = r0; k < out.row.size(); ++k) local[out.row[k]] = -1;
+    const int64_t nr = static_cast<int64_t>(out.row.size() - r0);
+    out.rows_max = std::max(out.rows_max, nr);
+    out.core_max = std::max<int64_t>(out.core_max, static_cast<int64_t>(core.size()));
+    out.ncore.push_back(static_cast<int32_t>(core.size()));
+    out.rptr.push_back(static_cast<int32_t>(out.row.size()));
+    ++out.n_blocks;
+  }
+  return true;
+}
+
 bool build_tile_plan(const HostMesh& m, int p, int64_t cap, TilePlan& out) {
   out = TilePlan();
   const int64_t nR = m.n_R, nP = m.n_P;

@@ -85,6 +85,23 @@ struct TilePlan {
   std::vector<double> minv;
 };
 
+// Blocks of two fused inner substeps (k_inner_pair).  The cores are the
+// nodes of R binned into square cells of R's bounding box whose side holds
+// about sqrt(bn) nodes (cells in row order, each core in Morton order); a
+// block's rows, row[rptr[b] .. rptr[b+1]), are its core (the first ncore[b])
+// and then its halo: the P nodes outside the core that neighbour a core node.
+// For every adjacency entry t of an R node i (adj_ptr[i] <= t < adj_ptr[i+1])
+// lidx[t] is the row of the neighbour among the rows of i's block, or -1 for
+// a neighbour off P.
+struct PairPlan {
+  int64_t n_blocks = 0, rows_max = 0, core_max = 0;
+  std::vector<int32_t> rptr, ncore, row;
+  std::vector<int16_t> lidx;
+};
+
+// false when R is empty, bn < 1 or a block's rows exceed 32767.
+bool build_pair_plan(const HostMesh& m, int bn, PairPlan& out);
+
 // Build the plan for tiles of at most `cap` computed nodes; false (and an
 // empty plan) when R is empty, p < 2, a tile would exceed 32000 nodes, no
 // cell size fits or a node has more than 15 slots beyond the fourth.

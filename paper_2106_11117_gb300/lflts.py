@@ -30,7 +30,7 @@ LFLTS_ERR_MESH = -6
 LFLTS_MEM_HOST = 0
 LFLTS_MEM_DEVICE = 1
 KERNEL_CLASSES = {"init": 0, "coarse": 1, "inner": 2, "qoi": 3, "sums": 4,
-                  "adj_inner": 5, "adj_edges": 6, "grad": 7}
+                  "adj_inner": 5, "adj_edges": 6, "grad": 7, "inner_pair": 8}
 
 EXPORTED = [
     "lflts_version", "lflts_create", "lflts_destroy", "lflts_last_error", "lflts_mesh_add",
@@ -47,6 +47,8 @@ LFLTS_OPT_FUSED_INNER = 5
 LFLTS_OPT_TILED_INNER = 6
 LFLTS_OPT_TILE_CAP = 7
 LFLTS_OPT_GRAPH_CACHE = 8
+LFLTS_OPT_PAIRED_INNER = 9
+LFLTS_OPT_PAIR_BLOCK = 10
 
 
 class LibraryNotBuilt(RuntimeError):

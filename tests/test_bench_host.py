@@ -68,9 +68,17 @@ def test_roofline_traffic_from_the_capture_of_the_current_kernels():
     cap = bench.CAPTURED["inner"]
     assert abs(r["traffic"] - cap["dram_bytes"] / cap["alg_bytes"] * 360e9 / 70) < 1.0
     assert 1.0 < r["traffic_over_alg"] < 2.0
-    saved = bench.CAPTURED["kernels_sha16"]
+    saved = cap["sha16"]
     try:
-        bench.CAPTURED["kernels_sha16"] = "0" * 16
+        cap["sha16"] = "0" * 16
         assert bench._roofline(prof, ("coarse", "inner"), names)["traffic"] is None
     finally:
-        bench.CAPTURED["kernels_sha16"] = saved
+        cap["sha16"] = saved
+
+
+def test_captured_traffic_matches_the_current_kernel_sources():
+    """Every captured figure names the sources it was taken with; the record
+    uses it only while their hash is unchanged."""
+    for cls, cap in bench.CAPTURED.items():
+        assert cap["src"] and len(cap["sha16"]) == 16, cls
+        assert 1.0 < cap["dram_bytes"] / cap["alg_bytes"] < 4.0, cls
