@@ -3,7 +3,9 @@
 This package generates *inputs only*: meshes (node coordinates, triangles,
 Dirichlet flags, the refinement mask P), the random-field basis evaluated at
 element centroids, the random draws xi, nodal initial data and the weights of
-the box-average quantity of interest.  It contains none of the method's
+the box-average quantity of interest; ``workload.channel`` the narrow channel
+of random width (reference mesh, vertex displacement mode, width draws,
+line-mean weights).  It contains none of the method's
 arithmetic (no mass or stiffness assembly, no time stepping, no MLMC
 estimator); those live independently in ``oracle/`` and in the CUDA library.
 """
