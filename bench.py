@@ -668,6 +668,72 @@ def run_lshape(args):
     print(json.dumps(line), flush=True)
 
 
+def run_channel(args):
+    """The narrow channel of random width (channel60-p25-b-uniform, Sec. 4.3):
+    3 levels of the reference mesh (H = 1/60, 1/120, 1/240; channel box
+    refined 25x; p = 100 substeps because the narrowest channel squeezes its
+    cells 4x), 256/64/16 level pairs, every draw's vertices moved by
+    Eq. MeshTransform and its stiffness and lumped mass formed on the GPU,
+    c = 1, Neumann boundary, QoI the mean of u(., 1) along x = -0.4.  One step
+    is the whole level-pair batch in one lflts_run_pairs call.  FP32 state,
+    FP64 QoI and sums."""
+    import numpy as np
+    import torch
+    from paper_2106_11117_gb300 import build, lflts
+    from workload.channel import CONFIG_CHANNEL as cfg, channel_level, xi_width
+    build.build()
+    torch.cuda.set_device(0)
+    ctx = lflts.Context(0)
+    hs = [ctx.add_level(channel_level(cfg, l)) for l in range(cfg.levels)]
+
+    def w(h):
+        return h.info["n_free"] + h.p * h.info["n_R"]
+
+    jobs, keep, units, h2d = [], [], 0, 0
+    for l in range(cfg.levels):
+        S = cfg.samples[l]
+        x = torch.from_numpy(xi_width(cfg.seed, l, S)).cuda()
+        o = [torch.zeros(S, dtype=torch.float64, device="cuda") for _ in range(2)]
+        o.append(torch.zeros(4, dtype=torch.float64, device="cuda"))
+        j = lflts.PairJob()
+        j.fine = hs[l].desc(cfg.precision)
+        if l:
+            j.coarse = hs[l - 1].desc(cfg.precision)
+            j.has_coarse = 1
+        j.xi, j.S = x.data_ptr(), S
+        j.dQ, j.Qf, j.sums = o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr()
+        jobs.append(j)
+        keep.append((x, o))
+        units += S * (hs[l].n_steps * w(hs[l]) + (hs[l - 1].n_steps * w(hs[l - 1]) if l else 0))
+        h2d += x.numel() * 8
+    jobs = (lflts.PairJob * len(jobs))(*jobs)
+    st = torch.cuda.current_stream()
+
+    def step():
+        lflts.lflts_run_pairs(ctx.h, jobs, lflts.LFLTS_MEM_DEVICE, st.cuda_stream)
+
+    ms, launches, clk, prof = _timed_passes(lflts, ctx, step, st, args.warmup, args.steps)
+    value = units * args.steps / (ms * 1e-3)
+    names = {"coarse": "k_coarse", "inner": INNER_NAME, "inner_pair": PAIR_NAME}
+    line = {"mode": "channel", "metric": UNIT + " (random-geometry channel)", "value": value,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{cfg.name}: two 0.95 x 1 rectangles joined by a 0.1 x b(w) channel, "
+                                   f"b ~ U(0.001, 0.007) mapped from the reference width 0.004 by moving "
+                                   f"the vertices, H = 1/{cfg.n0}..1/{cfg.n0 * 2 ** (cfg.levels - 1)}, "
+                                   f"channel box refined {cfg.p_mesh}x, p = {cfg.p_lts}, c = 1, Neumann, "
+                                   f"T = {cfg.T}, QoI mean of u along x = -0.4, samples "
+                                   f"{'/'.join(map(str, cfg.samples))} as fine/coarse pairs",
+                       "units_per_step": units, "mesh_nodes": [h.info["n_nodes"] for h in hs],
+                       "n_R": [h.info["n_R"] for h in hs], "n_steps": [h.n_steps for h in hs],
+                       "l2": "largest state below L2 (a few MB per array), no flush"},
+            "roofline": _roofline(prof, ("coarse", "inner", "inner_pair"), names), "gpu_launches": launches,
+            "clocks": clk, "kernel_classes": _classes_json(prof), "h2d_bytes_per_step": h2d,
+            "sums": [keep[l][1][2].cpu().tolist() for l in range(cfg.levels)]}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_adjoint(args):
     """dQ/dxi of every draw on square256-p8-K16 (256^2 base cells, box refined
     8x, 16 field terms, 1024 draws, 2000 outer steps of the CFL step, so
@@ -898,7 +964,7 @@ def main():
     ap.add_argument("--slices", type=int, default=20,
                     help="time slices per level-pair batch (one bench step = one slice)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["batched", "plain", "bandwidth", "lshape", "adjoint", "tte"],
+    ap.add_argument("--config", choices=["batched", "plain", "bandwidth", "lshape", "adjoint", "tte", "channel"],
                     default="batched")
     ap.add_argument("--eps-bw", type=float, default=1e-3, help="RMSE target on the bandwidth hierarchy")
     ap.add_argument("--eps-cls", type=float, default=2e-3, help="RMSE target, batched vs plain comparison")
@@ -932,6 +998,8 @@ def main():
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.config == "channel":
+        run_channel(args)
     elif args.config == "lshape":
         run_lshape(args)
     elif args.config == "adjoint":

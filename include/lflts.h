@@ -142,6 +142,31 @@ int lflts_mesh_add(lflts_ctx* ctx, const double* xy, int64_t n_nodes,
                    const uint8_t* P, const double* psi, int K, int* mesh_id);
 
 /*
+ * Register a mesh whose vertices move with the draw (Sec. 4.3): every draw is
+ * solved on this reference triangulation with vertex v moved to
+ *   x_v + sum_k xi_k D_k(v)
+ * (Eq. MeshTransform applied to the vertices; xi_k the draw's entries of the
+ * xi array a solve receives, K of them), with wave speed c = 1 and the
+ * stiffness and lumped mass of the moved mesh (Eq. waveeq_transformed): the
+ * solve forms, per draw and adjacency entry, K_ij / m_i of the moved
+ * elements.  Arguments as lflts_mesh_add, with
+ *   disp      [K][n_nodes][2] FP64 displacement modes D_k in the caller's
+ *             node order (copied)
+ *   K         number of modes, 1 <= K <= 16
+ * Every edge of the reference mesh is kept (a zero stiffness entry of the
+ * reference, such as the diagonal of a right triangle, is not zero once the
+ * vertices move).  Not supported on such a mesh: point sources,
+ * lflts_grad_xi and lflts_run_field_pair (LFLTS_ERR_ARG).  A draw that folds
+ * an element over (non-positive moved area) gives meaningless values; the
+ * caller keeps the modes and draws within the map's range.
+ * Errors: as lflts_mesh_add; LFLTS_ERR_ARG for disp == NULL or K outside
+ * [1, 16].
+ */
+int lflts_mesh_add_moving(lflts_ctx* ctx, const double* xy, int64_t n_nodes,
+                          const int32_t* tri, int64_t n_tri, const uint8_t* dirichlet,
+                          const uint8_t* P, const double* disp, int K, int* mesh_id);
+
+/*
  * Sizes of a registered mesh: info[0] n_nodes, [1] n_free (non-Dirichlet),
  * [2] n_R (nodes the inner substeps update: P and its element neighbours),
  * [3] n_P, [4] n_tri, [5] K, [6] n_edges (edges with a nonzero stiffness
@@ -170,7 +195,7 @@ int lflts_mesh_order(lflts_ctx* ctx, int mesh_id, int32_t* new2old);
  *   out[4+2(m-1)] beta_m = T_{m-1}/T_{m+1},
  *   out[5+2(m-1)] c_m = 2 dt^2 beta_{m+1/2} / omega.
  * out must hold 4 + 2(p-1) doubles.
- * Errors: LFLTS_ERR_ARG for out == NULL, p outside [1, 64], nu outside [0, 1] or dt <= 0.
+ * Errors: LFLTS_ERR_ARG for out == NULL, p outside [1, 128], nu outside [0, 1] or dt <= 0.
  */
 int lflts_lts_constants(int p, double nu, double dt, double* out);
 
@@ -227,7 +252,9 @@ typedef struct {
   int u0_field;     /* initial displacement, field id on the same mesh        */
   int v0_field;     /* initial velocity field id, or -1 for v0 = 0            */
   int precision;    /* 32: FP32 state, FP64 QoI; 64: FP64 throughout          */
-  int p;            /* LTS ratio, 1 <= p <= 64 (p = 1: leapfrog)             */
+  int p;            /* LTS ratio, 1 <= p <= 128 (p = 1: leapfrog; the fused,
+                       tiled and paired inner kernels and lflts_grad_xi take
+                       p <= 64)                                               */
   double nu;        /* stabilisation parameter, 0 <= nu <= 1                  */
   double dt;        /* coarse time step                                       */
   int64_t n_steps;  /* N >= 1 steps; the QoI is taken at t_N = N dt           */

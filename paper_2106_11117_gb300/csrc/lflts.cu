@@ -28,6 +28,7 @@
 #include "inner_tile.cuh"
 #include "kernels.cuh"
 #include "mesh_prep.h"
+#include "moving.cuh"
 
 using namespace lflts;
 
@@ -56,6 +57,17 @@ struct MeshGPU {
   float* psi32 = nullptr;
   double* psi64 = nullptr;
   int* new2old = nullptr;
+  // a mesh whose vertices move with the draw: the tables of k_moving_weights
+  int* dedge = nullptr;
+  int* tri_new = nullptr;
+  double* xy64 = nullptr;
+  double* disp = nullptr;
+  int* nptr = nullptr;
+  int* nelem = nullptr;
+  MovingDev moving() const {
+    return MovingDev{static_cast<int>(h.n_free), static_cast<int>(h.n_nodes), h.K_modes, adj_ptr, adj, dedge,
+                     ee, tri_new, xy64, disp, nptr, nelem};
+  }
   int* tri_dev = nullptr;    // caller's triangles and areas (L2(D)-valued QoI, uploaded on first use)
   double* area_dev = nullptr;
   // coupling slots of R for the fused inner kernel (built on first use)
@@ -1211,7 +1223,7 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   LF_TRY(ensure(c, ws.r1, r_bytes));
   LF_TRY(ensure(c, ws.r2, r_bytes));
   LF_TRY(ensure(c, ws.r3, r_bytes));
-  LF_TRY(ensure(c, ws.W, size_t(std::max<int64_t>(h.n_edges, 1)) * S * rb));
+  LF_TRY(ensure(c, ws.W, size_t(std::max<int64_t>(h.n_w, 1)) * S * rb));
   LF_TRY(ensure(c, ws.xipad, size_t(S) * KP * rb));
   LF_TRY(ensure(c, ws.qps, size_t(n_chunks) * S * sizeof(double)));
   LF_TRY(ensure(c, ws.qpc, size_t(n_chunks) * S * sizeof(double)));
@@ -1229,10 +1241,16 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
         n_nodes, (int)S, Sel<Real>::field(u0), v0 ? Sel<Real>::field(*v0) : nullptr, (Real)ds.dt, ua, ub, d,
         rg ? rg->d_dts : nullptr);
     LF_CUDA(c, cudaGetLastError());
-    const Geo ge = geometry(c, std::max<int64_t>(h.n_edges, 1), S);
-    k_edge_weights<Real, KP><<<ge.grid, 256, 0, st>>>(h.n_edges, (int)S, ge.SB, mg.ee, Sel<Real>::eg(mg),
-                                                      Sel<Real>::psi(mg), xi, W,
-                                                      rg ? static_cast<const Real*>(rg->d_sig) : nullptr);
+    if (h.moving) {  // stiffness and lumped mass of every draw's moved mesh
+      const Geo ge = geometry(c, std::max<int64_t>(h.n_free, 1), S);
+      k_moving_weights<Real><<<ge.grid, 256, 0, st>>>(mg.moving(), (int)S, ge.SB, d_xi, W,
+                                                       rg ? static_cast<const Real*>(rg->d_sig) : nullptr);
+    } else {
+      const Geo ge = geometry(c, std::max<int64_t>(h.n_edges, 1), S);
+      k_edge_weights<Real, KP><<<ge.grid, 256, 0, st>>>(h.n_edges, (int)S, ge.SB, mg.ee, Sel<Real>::eg(mg),
+                                                        Sel<Real>::psi(mg), xi, W,
+                                                        rg ? static_cast<const Real*>(rg->d_sig) : nullptr);
+    }
     LF_CUDA(c, cudaGetLastError());
     pr.end(LFLTS_KERNEL_INIT, double(S) * rb * 3.0 * n_nodes);  // u (twice) and d written
     c->launches += 2;  // three kernels in this class
@@ -1412,7 +1430,7 @@ int check_desc(lflts_ctx* c, const lflts_solve_desc* ds) {
   if (ds->v0_field >= 0 && (ds->v0_field >= (int)c->fields.size() || c->fields[ds->v0_field].mesh != ds->mesh_id))
     return fail(c, LFLTS_ERR_ARG, "solve: v0_field does not belong to the mesh");
   if (ds->precision != 32 && ds->precision != 64) return fail(c, LFLTS_ERR_ARG, "solve: precision must be 32 or 64");
-  if (ds->p < 1 || ds->p > 64) return fail(c, LFLTS_ERR_ARG, "solve: p must be in [1, 64]");
+  if (ds->p < 1 || ds->p > 128) return fail(c, LFLTS_ERR_ARG, "solve: p must be in [1, 128]");
   if (!(ds->nu >= 0.0 && ds->nu <= 1.0)) return fail(c, LFLTS_ERR_ARG, "solve: nu must be in [0, 1]");
   if (!(ds->dt > 0.0) || !std::isfinite(ds->dt)) return fail(c, LFLTS_ERR_ARG, "solve: dt must be positive");
   if (ds->n_steps < 1) return fail(c, LFLTS_ERR_ARG, "solve: n_steps must be >= 1");
@@ -1420,6 +1438,8 @@ int check_desc(lflts_ctx* c, const lflts_solve_desc* ds) {
     return fail(c, LFLTS_ERR_ARG, "solve: source_id does not belong to the mesh");
   if (ds->source_id >= 0 && !(std::isfinite(ds->src_f0) && std::isfinite(ds->src_t0) && std::isfinite(ds->src_amp)))
     return fail(c, LFLTS_ERR_ARG, "solve: non-finite source parameters");
+  if (ds->source_id >= 0 && c->meshes[ds->mesh_id]->h.moving)
+    return fail(c, LFLTS_ERR_ARG, "solve: a source on a moving mesh is not supported");
   return 0;
 }
 
@@ -1997,6 +2017,82 @@ int pairs_finish(lflts_ctx* c, PairRun& run, const lflts_pair_job* jobs, int n_j
   return LFLTS_OK;
 }
 
+// disp non-null: a mesh whose vertices move with the draw (K modes, psi unused)
+int mesh_add_impl(lflts_ctx* c, const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
+                  const uint8_t* dirichlet, const uint8_t* P, const double* psi, int K, const double* disp,
+                  int* mesh_id) {
+  if (!c || !mesh_id) return LFLTS_ERR_ARG;
+  c->err.clear();
+  std::unique_ptr<MeshGPU> mg(new MeshGPU());
+  std::vector<double> zero_psi;
+  if (disp) {
+    if (K < 1 || K > 16 || n_tri < 1) return fail(c, LFLTS_ERR_ARG, "mesh_add_moving: K must be in [1, 16]");
+    zero_psi.assign(static_cast<size_t>(n_tri) * K, 0.0);
+    psi = zero_psi.data();
+  }
+  int rc = prep_mesh(xy, n_nodes, tri, n_tri, dirichlet, P, psi, K, mg->h, c->err, disp != nullptr);
+  if (rc) return rc;
+  if (disp) {
+    rc = make_moving(mg->h, disp, K, c->err);
+    if (rc) return rc;
+  }
+  if (c->device >= 0) {
+    LF_TRY(set_device(c));
+    const HostMesh& h = mg->h;
+    const size_t na = h.adj_j.size(), ne = static_cast<size_t>(h.n_edges);
+    std::vector<int2> adj(na), ee(ne);
+    for (size_t t = 0; t < na; ++t) adj[t] = make_int2(h.adj_j[t], h.adj_e[t]);
+    std::vector<double> eg64(2 * ne);
+    for (size_t k = 0; k < ne; ++k) {
+      ee[k] = make_int2(h.edge_e0[k], h.edge_e1[k]);
+      eg64[2 * k] = h.edge_G0[k];
+      eg64[2 * k + 1] = h.edge_G1[k];
+    }
+    std::vector<float> eg32(eg64.begin(), eg64.end());
+    std::vector<float> minv32(h.minv.begin(), h.minv.end());
+    const double log2e = 1.4426950408889634073599246810019;
+    std::vector<float> psi32(h.psi.size());  // scaled by log2(e) for exp2f
+    for (size_t k = 0; k < psi32.size(); ++k) psi32[k] = float(h.psi[k] * log2e);
+    LF_TRY(upload(c, &mg->adj_ptr, h.adj_ptr.data(), h.adj_ptr.size()));
+    LF_TRY(upload(c, &mg->adj, adj.data(), na));
+    std::vector<int4> ell(static_cast<size_t>(h.n_free) * 2);
+    for (int64_t i = 0; i < h.n_free; ++i)
+      for (int hh = 0; hh < 2; ++hh)
+        ell[2 * i + hh] = make_int4(h.ell_j[4 * i + 2 * hh], h.ell_e[4 * i + 2 * hh], h.ell_j[4 * i + 2 * hh + 1],
+                                    h.ell_e[4 * i + 2 * hh + 1]);
+    LF_TRY(upload(c, &mg->ell, ell.data(), ell.size()));
+    if (!h.ell_hi_j.empty()) {
+      for (int64_t i = 0; i < h.n_free; ++i)
+        for (int hh = 0; hh < 2; ++hh)
+          ell[2 * i + hh] = make_int4(h.ell_hi_j[4 * i + 2 * hh], h.ell_hi_e[4 * i + 2 * hh],
+                                      h.ell_hi_j[4 * i + 2 * hh + 1], h.ell_hi_e[4 * i + 2 * hh + 1]);
+      LF_TRY(upload(c, &mg->ell_hi, ell.data(), ell.size()));
+    }
+    LF_TRY(upload(c, &mg->ee, ee.data(), ne));
+    std::vector<int2> ends(ne);
+    for (size_t k = 0; k < ne; ++k) ends[k] = make_int2(h.edge_i[k], h.edge_j[k]);
+    LF_TRY(upload(c, &mg->ends, ends.data(), ne));
+    LF_TRY(upload(c, &mg->eg32, eg32.data(), eg32.size()));
+    LF_TRY(upload(c, &mg->eg64, eg64.data(), eg64.size()));
+    LF_TRY(upload(c, &mg->minv32, minv32.data(), minv32.size()));
+    LF_TRY(upload(c, &mg->minv64, h.minv.data(), h.minv.size()));
+    LF_TRY(upload(c, &mg->psi32, psi32.data(), psi32.size()));
+    LF_TRY(upload(c, &mg->psi64, h.psi.data(), h.psi.size()));
+    LF_TRY(upload(c, &mg->new2old, h.new2old.data(), h.new2old.size()));
+    if (h.moving) {
+      LF_TRY(upload(c, &mg->dedge, h.dedge.data(), h.dedge.size()));
+      LF_TRY(upload(c, &mg->tri_new, h.tri_new.data(), h.tri_new.size()));
+      LF_TRY(upload(c, &mg->xy64, h.xy.data(), h.xy.size()));
+      LF_TRY(upload(c, &mg->disp, h.disp.data(), h.disp.size()));
+      LF_TRY(upload(c, &mg->nptr, h.nptr.data(), h.nptr.size()));
+      LF_TRY(upload(c, &mg->nelem, h.nelem.data(), h.nelem.size()));
+    }
+  }
+  *mesh_id = static_cast<int>(c->meshes.size());
+  c->meshes.push_back(std::move(mg));
+  return LFLTS_OK;
+}
+
 }  // namespace
 
 lflts_ctx::~lflts_ctx() = default;
@@ -2081,58 +2177,13 @@ const char* lflts_last_error(const lflts_ctx* c) { return c ? c->err.c_str() : "
 
 int lflts_mesh_add(lflts_ctx* c, const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
                    const uint8_t* dirichlet, const uint8_t* P, const double* psi, int K, int* mesh_id) {
-  if (!c || !mesh_id) return LFLTS_ERR_ARG;
-  c->err.clear();
-  std::unique_ptr<MeshGPU> mg(new MeshGPU());
-  int rc = prep_mesh(xy, n_nodes, tri, n_tri, dirichlet, P, psi, K, mg->h, c->err);
-  if (rc) return rc;
-  if (c->device >= 0) {
-    LF_TRY(set_device(c));
-    const HostMesh& h = mg->h;
-    const size_t na = h.adj_j.size(), ne = static_cast<size_t>(h.n_edges);
-    std::vector<int2> adj(na), ee(ne);
-    for (size_t t = 0; t < na; ++t) adj[t] = make_int2(h.adj_j[t], h.adj_e[t]);
-    std::vector<double> eg64(2 * ne);
-    for (size_t k = 0; k < ne; ++k) {
-      ee[k] = make_int2(h.edge_e0[k], h.edge_e1[k]);
-      eg64[2 * k] = h.edge_G0[k];
-      eg64[2 * k + 1] = h.edge_G1[k];
-    }
-    std::vector<float> eg32(eg64.begin(), eg64.end());
-    std::vector<float> minv32(h.minv.begin(), h.minv.end());
-    const double log2e = 1.4426950408889634073599246810019;
-    std::vector<float> psi32(h.psi.size());  // scaled by log2(e) for exp2f
-    for (size_t k = 0; k < psi32.size(); ++k) psi32[k] = float(h.psi[k] * log2e);
-    LF_TRY(upload(c, &mg->adj_ptr, h.adj_ptr.data(), h.adj_ptr.size()));
-    LF_TRY(upload(c, &mg->adj, adj.data(), na));
-    std::vector<int4> ell(static_cast<size_t>(h.n_free) * 2);
-    for (int64_t i = 0; i < h.n_free; ++i)
-      for (int hh = 0; hh < 2; ++hh)
-        ell[2 * i + hh] = make_int4(h.ell_j[4 * i + 2 * hh], h.ell_e[4 * i + 2 * hh], h.ell_j[4 * i + 2 * hh + 1],
-                                    h.ell_e[4 * i + 2 * hh + 1]);
-    LF_TRY(upload(c, &mg->ell, ell.data(), ell.size()));
-    if (!h.ell_hi_j.empty()) {
-      for (int64_t i = 0; i < h.n_free; ++i)
-        for (int hh = 0; hh < 2; ++hh)
-          ell[2 * i + hh] = make_int4(h.ell_hi_j[4 * i + 2 * hh], h.ell_hi_e[4 * i + 2 * hh],
-                                      h.ell_hi_j[4 * i + 2 * hh + 1], h.ell_hi_e[4 * i + 2 * hh + 1]);
-      LF_TRY(upload(c, &mg->ell_hi, ell.data(), ell.size()));
-    }
-    LF_TRY(upload(c, &mg->ee, ee.data(), ne));
-    std::vector<int2> ends(ne);
-    for (size_t k = 0; k < ne; ++k) ends[k] = make_int2(h.edge_i[k], h.edge_j[k]);
-    LF_TRY(upload(c, &mg->ends, ends.data(), ne));
-    LF_TRY(upload(c, &mg->eg32, eg32.data(), eg32.size()));
-    LF_TRY(upload(c, &mg->eg64, eg64.data(), eg64.size()));
-    LF_TRY(upload(c, &mg->minv32, minv32.data(), minv32.size()));
-    LF_TRY(upload(c, &mg->minv64, h.minv.data(), h.minv.size()));
-    LF_TRY(upload(c, &mg->psi32, psi32.data(), psi32.size()));
-    LF_TRY(upload(c, &mg->psi64, h.psi.data(), h.psi.size()));
-    LF_TRY(upload(c, &mg->new2old, h.new2old.data(), h.new2old.size()));
-  }
-  *mesh_id = static_cast<int>(c->meshes.size());
-  c->meshes.push_back(std::move(mg));
-  return LFLTS_OK;
+  return mesh_add_impl(c, xy, n_nodes, tri, n_tri, dirichlet, P, psi, K, nullptr, mesh_id);
+}
+
+int lflts_mesh_add_moving(lflts_ctx* c, const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
+                          const uint8_t* dirichlet, const uint8_t* P, const double* disp, int K, int* mesh_id) {
+  if (c && !disp) return fail(c, LFLTS_ERR_ARG, "mesh_add_moving: null displacement modes");
+  return mesh_add_impl(c, xy, n_nodes, tri, n_tri, dirichlet, P, nullptr, K, disp, mesh_id);
 }
 
 int lflts_mesh_info(lflts_ctx* c, int mesh_id, int64_t info[8]) {
@@ -2168,7 +2219,7 @@ int lflts_interp_weights(const double* xy_c, int64_t n_c, const int32_t* tri_c, 
 }
 
 int lflts_lts_constants(int p, double nu, double dt, double* out) {
-  if (!out || p < 1 || p > 64 || !(nu >= 0.0 && nu <= 1.0) || !(dt > 0.0)) return LFLTS_ERR_ARG;
+  if (!out || p < 1 || p > 128 || !(nu >= 0.0 && nu <= 1.0) || !(dt > 0.0)) return LFLTS_ERR_ARG;
   std::vector<double> beta, cm;
   double delta, omega, c0, gamma;
   lts_constants(p, nu, dt, beta, cm, delta, omega, c0, gamma);
@@ -2386,6 +2437,8 @@ int lflts_run_field_pair(lflts_ctx* c, const lflts_pair_job* jb, int interp_id, 
     return fail(c, LFLTS_ERR_ARG, "run_field_pair: null job, xi, sum_dU or sum_norm2, or S out of range");
   if (mem != LFLTS_MEM_HOST && mem != LFLTS_MEM_DEVICE) return fail(c, LFLTS_ERR_ARG, "run_field_pair: bad mem kind");
   LF_TRY(check_desc(c, &jb->fine));
+  if (c->meshes[jb->fine.mesh_id]->h.moving)
+    return fail(c, LFLTS_ERR_ARG, "run_field_pair: the L2(D) norm on a moving mesh is not supported");
   const Interp* in = nullptr;
   if (jb->has_coarse) {
     LF_TRY(check_desc(c, &jb->coarse));
@@ -2484,6 +2537,9 @@ int lflts_grad_xi(lflts_ctx* c, const lflts_solve_desc* ds, const double* xi, in
   c->err.clear();
   LF_TRY(set_device(c));
   LF_TRY(check_desc(c, ds));
+  if (c->meshes[ds->mesh_id]->h.moving)
+    return fail(c, LFLTS_ERR_ARG, "grad_xi: the gradient on a moving mesh is not supported");
+  if (ds->p > 64) return fail(c, LFLTS_ERR_ARG, "grad_xi: p must be in [1, 64]");
   if (S < 1 || S > kMaxS) return fail(c, LFLTS_ERR_ARG, "grad_xi: S must be in [1, 2097120]");
   if (!xi || !Q || !dQdxi) return fail(c, LFLTS_ERR_ARG, "grad_xi: null xi, Q or dQdxi");
   if (ckpt_every < 1) return fail(c, LFLTS_ERR_ARG, "grad_xi: ckpt_every must be >= 1");

@@ -20,7 +20,7 @@ uint64_t morton_spread16(uint64_t x) {  // interleave the low 16 bits with zeros
 
 int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
               const uint8_t* dirichlet, const uint8_t* P, const double* psi, int K,
-              HostMesh& out, std::string& err) {
+              HostMesh& out, std::string& err, bool keep_all_edges) {
   const int kErrArg = -1, kErrMesh = -6;
   if (!xy || !tri || !dirichlet || !psi || n_nodes < 3 || n_tri < 1) {
     err = "mesh_add: null array or empty mesh";
@@ -126,6 +126,11 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
   std::stable_sort(eorder.begin(), eorder.end(), [&](int32_t a, int32_t b) { return ekey[a] < ekey[b]; });
   std::vector<int32_t> enew(n_tri);
   for (int64_t k = 0; k < n_tri; ++k) enew[eorder[k]] = static_cast<int32_t>(k);
+  if (keep_all_edges) {  // element vertices in the new orders (a moving mesh needs them)
+    m.tri_new.resize(static_cast<size_t>(n_tri) * 3);
+    for (int64_t k = 0; k < n_tri; ++k)
+      for (int a = 0; a < 3; ++a) m.tri_new[3 * k + a] = m.old2new[tri[3 * eorder[k] + a]];
+  }
 
   // ---- psi, padded, in the new element order -------------------------------
   m.psi.assign(static_cast<size_t>(n_tri) * m.KP, 0.0);
@@ -181,7 +186,7 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
     }
     const bool any_free = rec[a].lo < m.n_free || rec[a].hi < m.n_free;
     const bool nonzero = rec[a].G != 0.0 || (b - a == 2 && rec[a + 1].G != 0.0);
-    if (any_free && nonzero) {
+    if (any_free && (nonzero || keep_all_edges)) {
       elo.push_back(rec[a].lo);
       ehi.push_back(rec[a].hi);
       m.edge_e0.push_back(rec[a].e);
@@ -192,6 +197,7 @@ int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_t
     a = b;
   }
   m.n_edges = static_cast<int64_t>(elo.size());
+  m.n_w = m.n_edges;
   m.edge_i = elo;
   m.edge_j = ehi;
   m.n_edges_P = 0;
@@ -412,6 +418,51 @@ void tile_nodes(const HostMesh& m, const std::vector<int32_t>& order, int64_t a0
 }
 
 }  // namespace
+
+int make_moving(HostMesh& m, const double* disp, int K, std::string& err) {
+  if (!disp || K < 1 || K > 16) {
+    err = "mesh_add_moving: null displacement modes or K outside [1, 16]";
+    return -1;
+  }
+  if (m.tri_new.size() != static_cast<size_t>(m.n_tri) * 3) {
+    err = "mesh_add_moving: mesh not prepared with every edge kept";
+    return -1;
+  }
+  const int64_t na = m.adj_ptr[m.n_free];
+  m.moving = true;
+  m.K_modes = K;
+  m.dedge.assign(m.adj_e.begin(), m.adj_e.end());
+  for (int64_t t = 0; t < na; ++t) m.adj_e[t] = static_cast<int32_t>(t);
+  for (int64_t i = 0; i < m.n_free; ++i) {
+    const int32_t a = m.adj_ptr[i], n = m.adj_ptr[i + 1] - a;
+    for (int q = 0; q < 4 && q < n; ++q) m.ell_e[4 * i + q] = a + q;
+    if (!m.ell_hi_e.empty())
+      for (int q = 0; q < 4 && q + 4 < n; ++q) m.ell_hi_e[4 * i + q] = a + 4 + q;
+  }
+  m.n_w = na;
+  // elements of every free node
+  std::vector<int32_t> cnt(m.n_free + 1, 0);
+  for (int64_t k = 0; k < m.n_tri; ++k)
+    for (int a = 0; a < 3; ++a)
+      if (m.tri_new[3 * k + a] < m.n_free) cnt[m.tri_new[3 * k + a] + 1]++;
+  m.nptr.assign(m.n_free + 1, 0);
+  for (int64_t i = 0; i < m.n_free; ++i) m.nptr[i + 1] = m.nptr[i] + cnt[i + 1];
+  m.nelem.assign(m.nptr[m.n_free], 0);
+  std::vector<int32_t> fill(m.nptr.begin(), m.nptr.end() - 1);
+  for (int64_t k = 0; k < m.n_tri; ++k)
+    for (int a = 0; a < 3; ++a) {
+      const int32_t v = m.tri_new[3 * k + a];
+      if (v < m.n_free) m.nelem[fill[v]++] = static_cast<int32_t>(k);
+    }
+  m.disp.assign(static_cast<size_t>(K) * m.n_nodes * 2, 0.0);
+  for (int k = 0; k < K; ++k)
+    for (int64_t v = 0; v < m.n_nodes; ++v)
+      for (int c = 0; c < 2; ++c)
+        m.disp[(static_cast<size_t>(k) * m.n_nodes + v) * 2 + c] =
+            disp[(static_cast<size_t>(k) * m.n_nodes + m.new2old[v]) * 2 + c];
+  m.minv.assign(m.n_free, 1.0);  // the weights carry 1 / m_i of the draw
+  return 0;
+}
 
 bool build_pair_plan(const HostMesh& m, int bn, PairPlan& out) {
   out = PairPlan();

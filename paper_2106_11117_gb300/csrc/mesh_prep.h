@@ -51,6 +51,18 @@ struct HostMesh {
   std::vector<double> xy;                  // [n_nodes][2] coordinates, internal order
   std::vector<int32_t> tri;                // [n_tri][3] vertices in the caller's numbering and order
   std::vector<double> area;                // [n_tri] |T| in the caller's element order
+  // rows of the per-draw coupling weights W: n_edges, or for a moving mesh
+  // one row per adjacency entry (directed: W[t] = K_ij / m_i of entry t)
+  int64_t n_w = 0;
+  // A mesh whose vertices move with the draw (make_moving): adj_e, ell_e and
+  // ell_hi_e hold adjacency entry ids, dedge[t] the undirected edge of entry
+  // t, tri_new the vertices (new ids) of every element in the new element
+  // order, nptr/nelem the elements of every free node, disp the K
+  // displacement modes [K][n_nodes][2] in the new node order; minv is 1.
+  bool moving = false;
+  int K_modes = 0;
+  std::vector<int32_t> dedge, tri_new, nptr, nelem;
+  std::vector<double> disp;
 };
 
 // Coupling slots of the inner substeps on R, in the order the per-substep
@@ -118,8 +130,15 @@ int64_t interp_weights(const double* xy_c, const int32_t* tri_c, int64_t n_tri_c
                        int64_t n_f, int32_t* vert, double* w, double tol);
 
 // Returns 0 on success; on failure fills err and returns a negative status.
+// keep_all_edges keeps the edges whose stiffness entries are all zero on the
+// given coordinates (needed when the coordinates change with the draw).
 int prep_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
               const uint8_t* dirichlet, const uint8_t* P, const double* psi, int K,
-              HostMesh& out, std::string& err);
+              HostMesh& out, std::string& err, bool keep_all_edges = false);
+
+// Turn a mesh prepared with keep_all_edges into one whose vertices move with
+// the draw by sum_k xi_k D_k (disp: [K][n_nodes][2] in the caller's node
+// order): directed weight rows, element and node-element tables, 1/m = 1.
+int make_moving(HostMesh& m, const double* disp, int K, std::string& err);
 
 }  // namespace lflts

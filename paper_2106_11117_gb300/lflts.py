@@ -39,7 +39,7 @@ EXPORTED = [
     "lflts_profile_enable", "lflts_profile_reset", "lflts_profile_read", "lflts_launch_count",
     "lflts_qoi_reduce_noalloc", "lflts_grad_xi", "lflts_set_option", "lflts_get_stats",
     "lflts_source_add", "lflts_interp_weights", "lflts_run_pairs_slice", "lflts_field_interp_add",
-    "lflts_run_field_pair", "lflts_graph_cache_size",
+    "lflts_run_field_pair", "lflts_graph_cache_size", "lflts_mesh_add_moving",
 ]
 LFLTS_OPT_GRAPHS = 1
 LFLTS_OPT_AUTOTUNE = 2
@@ -106,6 +106,7 @@ def load(path: str | None = None):
         "lflts_destroy": (i32, [vp]),
         "lflts_last_error": (C.c_char_p, [vp]),
         "lflts_mesh_add": (i32, [vp, vp, i64, vp, i64, vp, vp, vp, i32, C.POINTER(i32)]),
+        "lflts_mesh_add_moving": (i32, [vp, vp, i64, vp, i64, vp, vp, vp, i32, C.POINTER(i32)]),
         "lflts_mesh_info": (i32, [vp, i32, vp]),
         "lflts_mesh_order": (i32, [vp, i32, vp]),
         "lflts_lts_constants": (i32, [i32, C.c_double, C.c_double, vp]),
@@ -193,6 +194,21 @@ def lflts_mesh_add(ctx, xy, tri, dirichlet, P, psi):
     mid = C.c_int()
     _check(ctx, load().lflts_mesh_add(ctx, _ptr(xy), xy.shape[0], _ptr(tri), tri.shape[0],
                                       _ptr(dirichlet), _ptr(P), _ptr(psi), psi.shape[1], C.byref(mid)))
+    return mid.value
+
+
+def lflts_mesh_add_moving(ctx, xy, tri, dirichlet, P, disp):
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    dirichlet = np.ascontiguousarray(dirichlet, dtype=np.uint8)
+    P = None if P is None else np.ascontiguousarray(P, dtype=np.uint8)
+    disp = np.ascontiguousarray(disp, dtype=np.float64)
+    if disp.ndim != 3 or disp.shape[1:] != (xy.shape[0], 2):
+        raise ValueError("disp must be [K, n_nodes, 2]")
+    mid = C.c_int()
+    _check(ctx, load().lflts_mesh_add_moving(ctx, _ptr(xy), xy.shape[0], _ptr(tri), tri.shape[0],
+                                             _ptr(dirichlet), _ptr(P), _ptr(disp), disp.shape[0],
+                                             C.byref(mid)))
     return mid.value
 
 
@@ -384,7 +400,10 @@ class Context:
     def add_level(self, level: dict, P=True) -> LevelHandle:
         """Register a level built by the workload generators (mesh, psi, u0, QoI)."""
         m = level["mesh"]
-        mid = lflts_mesh_add(self.h, m.xy, m.tri, m.dirichlet, m.P if P else None, level["psi"])
+        if level.get("modes") is not None:  # vertices moved per draw by xi . modes
+            mid = lflts_mesh_add_moving(self.h, m.xy, m.tri, m.dirichlet, m.P if P else None, level["modes"])
+        else:
+            mid = lflts_mesh_add(self.h, m.xy, m.tri, m.dirichlet, m.P if P else None, level["psi"])
         qid = lflts_qoi_add(self.h, mid, level["qoi_idx"], level["qoi_w"])
         fid = lflts_field_add(self.h, mid, level["u0"])
         src = (-1, 0.0, 0.0, 0.0)

@@ -118,6 +118,28 @@ def test_host_only_mesh_preparation(lib):
         assert np.all(np.diff(z[order[a:b]].astype(np.int64)) >= 0)
 
 
+def test_host_only_moving_mesh_keeps_every_edge(lib):
+    """A mesh whose vertices move with the draw keeps the edges whose
+    stiffness is zero on the reference mesh (the "/" diagonals, nonzero once
+    the channel is squeezed) and refuses missing modes."""
+    from workload.channel import channel_mesh, displacement_mode
+    m = channel_mesh(20, 0)
+    ctx = lib.lflts_create(-1)
+    try:
+        fixed = lib.lflts_mesh_info(ctx, lib.lflts_mesh_add(ctx, m.xy, m.tri, m.dirichlet, m.P,
+                                                            np.zeros((m.n_tri, 1))))
+        moving = lib.lflts_mesh_info(ctx, lib.lflts_mesh_add_moving(ctx, m.xy, m.tri, m.dirichlet, m.P,
+                                                                    displacement_mode(m)[None]))
+        with pytest.raises(ValueError):
+            lib.lflts_mesh_add_moving(ctx, m.xy, m.tri, m.dirichlet, m.P, displacement_mode(m))
+    finally:
+        lib.lflts_destroy(ctx)
+    e = np.sort(np.concatenate([m.tri[:, [0, 1]], m.tri[:, [1, 2]], m.tri[:, [2, 0]]]), axis=1)
+    n_all = np.unique(e, axis=0).shape[0]
+    assert moving["n_edges"] == n_all > fixed["n_edges"]
+    assert moving["K"] == 1 and moving["n_R"] == fixed["n_R"] and moving["n_free"] == m.n_nodes
+
+
 def test_invalid_mesh_rejected(lib):
     ctx = lib.lflts_create(-1)
     try:
