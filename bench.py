@@ -536,8 +536,9 @@ def _classes_json(prof):
             for k, v in prof.items() if v["launches"]}
 
 
-def _alg1_run(lflts, mlmc, ctx, hs, cfg, eps, plain, L_max, n_init, seed_off=0):
-    """Alg. 1 on the given level handles with the workload's draws; wall time."""
+def _alg1_run(lflts, mlmc, ctx, hs, cfg, eps, plain, L_max, n_init, seed_off=0, draw=None):
+    """Alg. 1 on the given level handles with the workload's draws (or
+    draw(l, offset, n)); wall time."""
     from workload import xi_uniform
 
     def w(h):
@@ -546,8 +547,9 @@ def _alg1_run(lflts, mlmc, ctx, hs, cfg, eps, plain, L_max, n_init, seed_off=0):
     def cost(l):
         return float(w(hs[l]) + (w(hs[l - 1]) if l else 0))
 
-    def draw(l, off, n):
-        return xi_uniform(cfg.seed + seed_off, l, n, cfg.K, offset=off)
+    if draw is None:
+        def draw(l, off, n):
+            return xi_uniform(cfg.seed + seed_off, l, n, cfg.K, offset=off)
 
     ev = mlmc.GpuLevelPairs(lflts, ctx, hs, precision=32, plain=plain)
     r = mlmc.alg1(ev, draw, eps, cost, lambda l: n_init, L_max=L_max)
@@ -715,6 +717,13 @@ def run_channel(args):
     ms, launches, clk, prof = _timed_passes(lflts, ctx, step, st, args.warmup, args.steps)
     value = units * args.steps / (ms * 1e-3)
     names = {"coarse": "k_coarse", "inner": INNER_NAME, "inner_pair": PAIR_NAME}
+    tte = None
+    if not args.no_time_to_eps:  # Alg. 1 on the three levels, draws of their own
+        from paper_2106_11117_gb300 import mlmc
+        torch.cuda.synchronize()
+        tte = _alg1_run(lflts, mlmc, ctx, hs, cfg, args.eps_channel, False, cfg.levels - 1, 64,
+                        draw=lambda l, off, n: xi_width(cfg.seed + 77, l, n, offset=off))
+        tte["eps"] = args.eps_channel
     line = {"mode": "channel", "metric": UNIT + " (random-geometry channel)", "value": value,
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -729,7 +738,7 @@ def run_channel(args):
                        "l2": "largest state below L2 (a few MB per array), no flush"},
             "roofline": _roofline(prof, ("coarse", "inner", "inner_pair"), names), "gpu_launches": launches,
             "clocks": clk, "kernel_classes": _classes_json(prof), "h2d_bytes_per_step": h2d,
-            "sums": [keep[l][1][2].cpu().tolist() for l in range(cfg.levels)]}
+            "sums": [keep[l][1][2].cpu().tolist() for l in range(cfg.levels)], "time_to_eps": tte}
     ctx.close()
     print(json.dumps(line), flush=True)
 
@@ -968,6 +977,7 @@ def main():
                     default="batched")
     ap.add_argument("--eps-bw", type=float, default=1e-3, help="RMSE target on the bandwidth hierarchy")
     ap.add_argument("--eps-cls", type=float, default=2e-3, help="RMSE target, batched vs plain comparison")
+    ap.add_argument("--eps-channel", type=float, default=2e-5, help="RMSE target on the channel hierarchy")
     ap.add_argument("--tte-levels", type=int, default=3, help="levels of square128-p8-K8 in the comparison")
     ap.add_argument("--tte-n-init", type=int, default=64, help="initial samples per level of Alg. 1")
     ap.add_argument("--tte-skip-plain", action="store_true")

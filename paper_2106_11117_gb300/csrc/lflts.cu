@@ -1058,7 +1058,7 @@ std::unique_ptr<SliceTask> make_sliced(lflts_ctx* c, const lflts_solve_desc& ds,
 // limit (outside any graph capture).
 template <typename Real>
 bool pair_ok(lflts_ctx* c, MeshGPU& mg, int n_R, int64_t S, int p) {
-  if (n_R < 1 || p < 3 || p > 64 || S < 1) return false;
+  if (n_R < 1 || p < 3 || p > 128 || S < 1) return false;
   auto it = mg.pairs.find(c->pair_block);
   if (it == mg.pairs.end()) {
     MeshGPU::DevPairs dp;
