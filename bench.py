@@ -207,8 +207,14 @@ def setup_gpu(cfg, rank, n_slices, autotune=True):
     from workload import level_problem, xi_uniform
     build.build()
     ctx = lflts.Context(torch.cuda.current_device())
-    if not autotune:  # the default launch shapes (for a launch list under a profiler)
+    if not autotune:
+        # for a launch list under a profiler (whose serialisation would skew
+        # the autotuner's timings): the inner kernels the autotuner picks for
+        # this hierarchy on GB300, paired substeps where |R| >= 500,000
+        # (levels 3 and 4 of square128-p8-K8-L5), default shapes otherwise
         lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_AUTOTUNE, 0)
+        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_PAIRED_INNER, 2)
+        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_PAIR_MIN_R, 500000)
     hs = []
     for l in range(cfg.levels):
         lev = level_problem(cfg, l)
@@ -984,7 +990,8 @@ def main():
     ap.add_argument("--tte-skip-bw", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="default launch shapes (the autotuner's timings are not valid under a profiler)")
+                    help="fixed launch shapes (the autotuner's timings are not valid under a profiler): "
+                         "the inner kernels the autotuner picks on GB300, default shapes otherwise")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cores", type=int, default=0)
     ap.add_argument("--cpu-rounds", type=int, default=8,

@@ -101,9 +101,12 @@ enum {
                                  0 never; 1 (default) autotuned where |R| > 2048 (4 draws per thread
                                  in FP32, 2 in FP64); always where the blocks fit in shared memory
                                  with 2: 4 draws per thread in FP32, 2 in FP64; 3: 2; 4: 1 */
-  LFLTS_OPT_PAIR_BLOCK = 10   /* about this many nodes of R per block of the paired substeps,
+  LFLTS_OPT_PAIR_BLOCK = 10,  /* about this many nodes of R per block of the paired substeps,
                                  16..4096 (default 144); blocks whose rows do not fit in the shared
                                  memory of a CTA make the batch run one launch per substep */
+  LFLTS_OPT_PAIR_MIN_R = 11   /* with LFLTS_OPT_PAIRED_INNER >= 2: forced only on meshes with at least
+                                 this many nodes of R (default 0: every mesh); fixes the shapes a
+                                 profiler run uses without timing them */
 };
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -469,7 +472,8 @@ int lflts_graph_cache_size(lflts_ctx* ctx, int64_t* n);
  * Errors: LFLTS_ERR_ARG for a NULL context, an unknown option, a fused-inner mode
  * outside {0, 1, 2}, a tiled-inner mode outside {0, 1, 2}, a tile capacity
  * in [1, 15] or negative, a graph cache below 1, a paired-inner mode outside
- * 0..4 or a paired-substep block outside [16, 4096]. */
+ * 0..4, a paired-substep block outside [16, 4096] or a negative paired-substep
+ * minimum |R|. */
 int lflts_set_option(lflts_ctx* ctx, int option, int64_t value);
 
 /*

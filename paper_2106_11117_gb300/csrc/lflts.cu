@@ -200,6 +200,7 @@ struct lflts_ctx {
   int64_t tile_cap = 0;          // > 0: at most this many computed nodes per tile
   int pair_mode = 1;             // paired inner substeps: 0 never, 1 autotuned, 2 always where they fit
   int pair_block = 144;          // about this many nodes of R per block of the paired substeps
+  int64_t pair_min_r = 0;        // forced paired substeps only where |R| is at least this
   std::vector<void*> owned;  // device allocations of meshes, fields, QoIs
   std::unique_ptr<PairRun> run;  // lflts_run_pairs_slice: the run in progress, if any
   std::vector<Interp> interps;   // lflts_field_interp_add
@@ -1110,7 +1111,7 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
     if (S % v == 0) vecs.push_back(v);
   vec = vecs.front();
   cps = 16;
-  if (c->pair_mode >= 2 && !dts && pair_ok<Real>(c, mg, n_R, S, ds.p)) {
+  if (c->pair_mode >= 2 && !dts && n_R >= c->pair_min_r && pair_ok<Real>(c, mg, n_R, S, ds.p)) {
     // 2: 4 draws per thread in FP32, 2 in FP64; 3: 2; 4: 1
     const int kind = c->pair_mode == 2 ? (sizeof(Real) == 4 ? 5 : 6) : c->pair_mode + 3;
     if (S % pair_vec_of_kind<Real>(kind) == 0) {
@@ -2624,6 +2625,11 @@ int lflts_set_option(lflts_ctx* c, int option, int64_t value) {
       if (value < 16 || value > 4096)
         return fail(c, LFLTS_ERR_ARG, "set_option: paired-substep block must be 16..4096 nodes");
       c->pair_block = static_cast<int>(value);
+      for (auto& m : c->meshes) m->tuned.clear();
+      return LFLTS_OK;
+    case LFLTS_OPT_PAIR_MIN_R:
+      if (value < 0) return fail(c, LFLTS_ERR_ARG, "set_option: paired-substep minimum |R| must be >= 0");
+      c->pair_min_r = value;
       for (auto& m : c->meshes) m->tuned.clear();
       return LFLTS_OK;
     case LFLTS_OPT_GRAPH_CACHE:

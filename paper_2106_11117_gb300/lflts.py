@@ -49,6 +49,7 @@ LFLTS_OPT_TILE_CAP = 7
 LFLTS_OPT_GRAPH_CACHE = 8
 LFLTS_OPT_PAIRED_INNER = 9
 LFLTS_OPT_PAIR_BLOCK = 10
+LFLTS_OPT_PAIR_MIN_R = 11
 
 
 class LibraryNotBuilt(RuntimeError):
