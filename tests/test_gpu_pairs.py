@@ -88,3 +88,28 @@ def test_paired_substeps_fullsize_mesh_against_oracle(lf):
     np.testing.assert_array_equal(Up, U0)
     Qo, Uo = oracle_run(lev, xi[:2])
     assert rel_err(Up[:, :2], Uo) <= 1e-5
+
+
+def test_forced_pairs_respect_the_minimum_R(lf):
+    """LFLTS_OPT_PAIR_MIN_R: forced paired substeps only on meshes whose R
+    has at least that many nodes; the values stay the same either way."""
+    lev = small_level(n=16, p=5, K=4, box=(0.3, 0.7, 0.3, 0.7))
+    xi = draws(8, 4, seed=5)
+    Q0, U0, l0, h = _solve(lf, lev, xi, 32, 0)
+    n_R = h.info["n_R"]
+    for min_r, paired in ((n_R + 1, False), (n_R, True)):
+        ctx = lf.Context(0)
+        try:
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_AUTOTUNE, 0)
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_FUSED_INNER, 0)
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_TILED_INNER, 0)
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_PAIRED_INNER, 2)
+            lf.lflts_set_option(ctx.h, lf.LFLTS_OPT_PAIR_MIN_R, min_r)
+            hh = ctx.add_level(lev)
+            n0 = lf.lflts_launch_count(ctx.h)
+            Q, U = ctx.solve(hh, xi, precision=32, state=True)
+            launches = lf.lflts_launch_count(ctx.h) - n0
+        finally:
+            ctx.close()
+        np.testing.assert_array_equal(U, U0)
+        assert (launches < l0) == paired
