@@ -477,8 +477,23 @@ bool build_pair_plan(const HostMesh& m, int bn, PairPlan& out) {
     y1 = std::max(y1, m.xy[2 * i + 1]);
   }
   const double wx = std::max(x1 - x0, 1e-300), wy = std::max(y1 - y0, 1e-300);
-  // a cell of side L holds about (L / h)^2 nodes where R fills its box
-  const double h = std::sqrt(wx * wy / double(nR));
+  // node spacing of the densest part of R: the median over R of each node's
+  // shortest edge; a cell of side L there holds about (L / h)^2 nodes
+  std::vector<double> hmin;
+  hmin.reserve(static_cast<size_t>(nR));
+  for (int64_t i = 0; i < nR; ++i) {
+    double best = 1e300;
+    for (int32_t t = m.adj_ptr[i]; t < m.adj_ptr[i + 1]; ++t) {
+      const int32_t j = m.adj_j[t];
+      best = std::min(best, std::hypot(m.xy[2 * j] - m.xy[2 * i], m.xy[2 * j + 1] - m.xy[2 * i + 1]));
+    }
+    if (best < 1e300) hmin.push_back(best);
+  }
+  double h = std::sqrt(wx * wy / double(nR));
+  if (!hmin.empty()) {
+    std::nth_element(hmin.begin(), hmin.begin() + hmin.size() / 2, hmin.end());
+    h = hmin[hmin.size() / 2];
+  }
   const double L = std::max(h, std::sqrt(double(bn)) * h);
   const int64_t ncx = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(wx / L))),
                 ncy = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(wy / L)));

@@ -98,8 +98,10 @@ struct TilePlan {
 };
 
 // Blocks of two fused inner substeps (k_inner_pair).  The cores are the
-// nodes of R binned into square cells of R's bounding box whose side holds
-// about sqrt(bn) nodes (cells in row order, each core in Morton order); a
+// nodes of R binned into square cells of R's bounding box of side sqrt(bn)
+// times the median over R of each node's shortest edge, so that a cell of a
+// uniform part of R holds about bn nodes (cells in row order, each core in
+// Morton order); a
 // block's rows, row[rptr[b] .. rptr[b+1]), are its core (the first ncore[b])
 // and then its halo: the P nodes outside the core that neighbour a core node.
 // For every adjacency entry t of an R node i (adj_ptr[i] <= t < adj_ptr[i+1])
