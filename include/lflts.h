@@ -104,9 +104,17 @@ enum {
   LFLTS_OPT_PAIR_BLOCK = 10,  /* about this many nodes of R per block of the paired substeps,
                                  16..4096 (default 144); blocks whose rows do not fit in the shared
                                  memory of a CTA make the batch run one launch per substep */
-  LFLTS_OPT_PAIR_MIN_R = 11   /* with LFLTS_OPT_PAIRED_INNER >= 2: forced only on meshes with at least
+  LFLTS_OPT_PAIR_MIN_R = 11,  /* with LFLTS_OPT_PAIRED_INNER >= 2: forced only on meshes with at least
                                  this many nodes of R (default 0: every mesh); fixes the shapes a
                                  profiler run uses without timing them */
+  LFLTS_OPT_COARSE_RC = 12    /* the coarse launch forms the coupling weights it needs from xi and
+                                 the field basis (Sec. 3.2: the field at the quadrature points is
+                                 a lower-order cost) instead of reading the stored per-draw weights;
+                                 same values bit for bit; uniform batches of fixed meshes with at
+                                 most four table neighbours: 0 (default) never, because on GB300
+                                 it measured 3x slower than reading the stored weights (issue-bound:
+                                 eight exp2 and 72 FMA per node and draw); 1 timed against the
+                                 stored weights; 2 always where it applies */
 };
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -472,8 +480,8 @@ int lflts_graph_cache_size(lflts_ctx* ctx, int64_t* n);
  * Errors: LFLTS_ERR_ARG for a NULL context, an unknown option, a fused-inner mode
  * outside {0, 1, 2}, a tiled-inner mode outside {0, 1, 2}, a tile capacity
  * in [1, 15] or negative, a graph cache below 1, a paired-inner mode outside
- * 0..4, a paired-substep block outside [16, 4096] or a negative paired-substep
- * minimum |R|. */
+ * 0..4, a paired-substep block outside [16, 4096], a negative paired-substep
+ * minimum |R| or a coarse weight mode outside {0, 1, 2}. */
 int lflts_set_option(lflts_ctx* ctx, int option, int64_t value);
 
 /*

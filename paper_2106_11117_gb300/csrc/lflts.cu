@@ -23,6 +23,7 @@
 
 #include "../../include/lflts.h"
 #include "adjoint.cuh"
+#include "coarse_rc.cuh"
 #include "field_qoi.cuh"
 #include "inner_pair.cuh"
 #include "inner_tile.cuh"
@@ -76,6 +77,8 @@ struct MeshGPU {
   int64_t n_rslots = -1;
   // autotuned (vec, shape code) per (S, precision, p)
   std::map<std::tuple<int64_t, int, int>, std::pair<int, int>> tuned;
+  // whether the coarse launch forms its weights (k_coarse_rc), per (S, precision, p)
+  std::map<std::tuple<int64_t, int, int>, bool> tuned_rc;
   // tile plans of the on-chip inner substeps per (p, tile capacity), uploaded
   struct DevTiles {
     TileDev dev{};
@@ -201,6 +204,7 @@ struct lflts_ctx {
   int pair_mode = 1;             // paired inner substeps: 0 never, 1 autotuned, 2 always where they fit
   int pair_block = 144;          // about this many nodes of R per block of the paired substeps
   int64_t pair_min_r = 0;        // forced paired substeps only where |R| is at least this
+  int coarse_rc = 0;             // coarse launch forming its weights: 0 never (measured slower), 1 timed, 2 always
   std::vector<void*> owned;  // device allocations of meshes, fields, QoIs
   std::unique_ptr<PairRun> run;  // lflts_run_pairs_slice: the run in progress, if any
   std::vector<Interp> interps;   // lflts_field_interp_add
@@ -547,6 +551,12 @@ struct Stepper {
   int fSB = 1;
   size_t fsmem = 0;
   int fgrid = 1;
+  // coarse launch forming the coupling weights from xi (k_coarse_rc), with
+  // its own draws per thread, or the stored weights (k_coarse)
+  bool crc = false;
+  Geo gcr{};
+  int KPs = 0;                  // padded field terms of the mesh
+  const Real* xi_pad = nullptr;  // [S][KP] draws (set by the loop that owns the workspace)
   int pvec = 0;  // inner substeps two by two (k_inner_pair) with pvec draws per thread, or 0
   PairDev pdev{};
   size_t psmem = 0;
@@ -575,6 +585,9 @@ struct Stepper {
     // +2000 for the fused inner kernel, +3000 for the tiled one, +5000 for
     // the paired substeps with 4 draws per thread (+6000: 2, +7000: 1; they
     // need the fourth r buffer r3)
+    // +10000: the coarse launch forms its coupling weights (k_coarse_rc)
+    crc = shape >= 10000;
+    shape %= 10000;
     minb6 = (shape % 1000) >= 100;
     const int cta_per_sm = shape % 100;
     cps = cta_per_sm;
@@ -593,6 +606,9 @@ struct Stepper {
     lts_constants(p, ds.nu, ds.dt, beta, cm, delta, omega, c0, gamma);
     md = Sel<Real>::mesh(mg, n_R);
     gc = geometry_vec(c, h.n_free, S, VEC, cta_per_sm);
+    KPs = h.KP;
+    if (crc && (h.moving || mg.ell_hi || S % 2 != 0)) crc = false;
+    if (crc) gcr = geometry_vec(c, h.n_free, S, 2, cta_per_sm);
     gi = geometry_vec(c, std::max(n_R, 1), S, VEC, cta_per_sm);
     Srb = double(S) * sizeof(Real);
     coarse_bytes = 3.0 * Srb * double(h.n_free);
@@ -681,7 +697,18 @@ struct Stepper {
 #define LF_COARSE_H(B, RG)         \
   if (md.ell_hi) LF_COARSE(B, RG, true); \
   else LF_COARSE(B, RG, false)
-      if (dts) {  // ragged batch (bounded to 64 registers: four CTAs of 256 per SM)
+      if (crc && !dts && xi_pad) {  // weights formed in the kernel (2 draws per thread)
+        const MeshGPU& mg = *mgp;
+        if (KPs == 4)
+          k_coarse_rc<Real, 2, 4><<<gcr.grid, 256, 0, st>>>(md, (int)S, gcr.SB, mg.ee, Sel<Real>::eg(mg),
+                                                            Sel<Real>::psi(mg), xi_pad, uc, un, d, g, kg, fw, fa);
+        else if (KPs == 8)
+          k_coarse_rc<Real, 2, 8><<<gcr.grid, 256, 0, st>>>(md, (int)S, gcr.SB, mg.ee, Sel<Real>::eg(mg),
+                                                            Sel<Real>::psi(mg), xi_pad, uc, un, d, g, kg, fw, fa);
+        else
+          k_coarse_rc<Real, 2, 16><<<gcr.grid, 256, 0, st>>>(md, (int)S, gcr.SB, mg.ee, Sel<Real>::eg(mg),
+                                                             Sel<Real>::psi(mg), xi_pad, uc, un, d, g, kg, fw, fa);
+      } else if (dts) {  // ragged batch (bounded to 64 registers: four CTAs of 256 per SM)
         if (minb6) LF_COARSE_H(6, true);
         else LF_COARSE_H(4, true);
       } else {
@@ -806,6 +833,7 @@ int time_loop(lflts_ctx* c, const lflts_solve_desc& ds, const MeshGPU& mg, int n
                          static_cast<Real*>(ws.r0.p), static_cast<Real*>(ws.r1.p), static_cast<Real*>(ws.r2.p),
                          cta_per_sm, static_cast<Real*>(ws.r3.p));
   stp.dts = dts;  // a ragged batch: its kernels (all draws active)
+  stp.xi_pad = static_cast<const Real*>(ws.xipad.p);
   Real* uc = static_cast<Real*>(ws.ua.p);
   Real* un = static_cast<Real*>(ws.ub.p);
   Real* d = static_cast<Real*>(ws.d.p);
@@ -1001,6 +1029,7 @@ struct SlicedLoop : SliceTask {
         N(ds.n_steps),
         st(st_),
         out(std::move(o)) {
+    stp.xi_pad = static_cast<const Real*>(ws.xipad.p);
     if (rg) {
       segs = rg->segs;
       stp.dts = rg->d_dts;
@@ -1103,8 +1132,8 @@ bool pair_ok(lflts_ctx* c, MeshGPU& mg, int n_R, int64_t S, int p) {
 }
 
 template <typename Real>
-int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
-                 cudaStream_t st, int& vec, int& cps, const double* dts) {
+int launch_shape_base(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
+                      cudaStream_t st, int& vec, int& cps, const double* dts) {
   const int vmax = (sizeof(Real) == 4) ? 4 : 2;
   std::vector<int> vecs;
   for (int v = vmax; v >= 1; v /= 2)
@@ -1198,6 +1227,55 @@ int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   mg.tuned[key] = std::make_pair(vec, cps);
+  return 0;
+}
+
+// Launch shape of a solve: draws per thread and shape code (launch_shape_base),
+// then whether the coarse launch forms its coupling weights in the kernel
+// (+10000, k_coarse_rc): always with LFLTS_OPT_COARSE_RC = 2, timed against
+// the stored weights once per (S, precision, p) with 1.
+template <typename Real>
+int launch_shape(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
+                 cudaStream_t st, int& vec, int& cps, const double* dts) {
+  LF_TRY(launch_shape_base<Real>(c, ds, mg, n_R, S, ws, st, vec, cps, dts));
+  const bool eligible = c->coarse_rc > 0 && !dts && !mg.h.moving && !mg.ell_hi && S % 2 == 0 && cps < 10000;
+  if (!eligible) return 0;
+  if (c->coarse_rc == 2) {
+    cps += 10000;
+    return 0;
+  }
+  if (!c->autotune) return 0;
+  const auto key = std::make_tuple(S, ds.precision, ds.p);
+  auto it = mg.tuned_rc.find(key);
+  if (it == mg.tuned_rc.end()) {
+    cudaEvent_t e0, e1;
+    LF_CUDA(c, cudaEventCreate(&e0));
+    LF_CUDA(c, cudaEventCreate(&e1));
+    const bool prof = c->profiling;
+    c->profiling = false;
+    const int64_t launches0 = c->launches;
+    const int64_t steps = std::min<int64_t>(4, ds.n_steps);
+    float t[2] = {0.f, 0.f};
+    int rc = 0;
+    for (int a = 0; a < 2 && !rc; ++a) {
+      Real* uc = nullptr;
+      const int k = cps + 10000 * a;
+      rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, vec, k, 1, dts);  // warm
+      if (!rc) rc = cudaEventRecord(e0, st) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
+      if (!rc) rc = time_loop_vec<Real>(c, ds, mg, n_R, S, ws, uc, st, vec, k, steps, dts);
+      if (!rc) rc = cudaEventRecord(e1, st) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
+      if (!rc) rc = cudaEventSynchronize(e1) == cudaSuccess ? 0 : LFLTS_ERR_CUDA;
+      if (!rc) cudaEventElapsedTime(&t[a], e0, e1);
+    }
+    c->tune_launches += c->launches - launches0;
+    c->launches = launches0;
+    c->profiling = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    it = mg.tuned_rc.emplace(key, t[1] < t[0]).first;
+  }
+  if (it->second) cps += 10000;
   return 0;
 }
 
@@ -1318,7 +1396,8 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   // (more than kGraphMaxKernels kernels) launch directly: their graphs would
   // take seconds and gigabytes of host memory to build, and their kernels
   // outlast the launch cost anyway.
-  const int64_t inner_per_step = n_R == 0 ? 0 : (cps >= 5000 ? p / 2 : (cps >= 2000 ? 1 : p - 1));
+  const int shape_in = cps % 10000;  // the inner kernel's part of the shape code
+  const int64_t inner_per_step = n_R == 0 ? 0 : (shape_in >= 5000 ? p / 2 : (shape_in >= 2000 ? 1 : p - 1));
   const int64_t est_kernels = ds.n_steps * (1 + inner_per_step);
   const bool use_graph =
       allow_graph && c->graphs && !c->profiling && st != nullptr && est_kernels <= kGraphMaxKernels;
@@ -2626,6 +2705,14 @@ int lflts_set_option(lflts_ctx* c, int option, int64_t value) {
         return fail(c, LFLTS_ERR_ARG, "set_option: paired-substep block must be 16..4096 nodes");
       c->pair_block = static_cast<int>(value);
       for (auto& m : c->meshes) m->tuned.clear();
+      return LFLTS_OK;
+    case LFLTS_OPT_COARSE_RC:
+      if (value < 0 || value > 2) return fail(c, LFLTS_ERR_ARG, "set_option: coarse weight mode must be 0, 1 or 2");
+      c->coarse_rc = static_cast<int>(value);
+      for (auto& m : c->meshes) {
+        m->tuned.clear();
+        m->tuned_rc.clear();
+      }
       return LFLTS_OK;
     case LFLTS_OPT_PAIR_MIN_R:
       if (value < 0) return fail(c, LFLTS_ERR_ARG, "set_option: paired-substep minimum |R| must be >= 0");

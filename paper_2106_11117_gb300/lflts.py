@@ -50,6 +50,7 @@ LFLTS_OPT_GRAPH_CACHE = 8
 LFLTS_OPT_PAIRED_INNER = 9
 LFLTS_OPT_PAIR_BLOCK = 10
 LFLTS_OPT_PAIR_MIN_R = 11
+LFLTS_OPT_COARSE_RC = 12
 
 
 class LibraryNotBuilt(RuntimeError):
