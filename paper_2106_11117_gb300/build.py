@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "liblflts.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lflts.cu", "qoi_noalloc.cu", "mesh_prep.cpp"]
-DEPS = SOURCES + ["kernels.cuh", "inner_tile.cuh", "inner_pair.cuh", "moving.cuh", "coarse_rc.cuh", "field_qoi.cuh", "adjoint.cuh", "mesh_prep.h"]
+DEPS = SOURCES + ["kernels.cuh", "inner_tile.cuh", "inner_pair.cuh", "moving.cuh", "coarse_rc.cuh", "restride.cuh", "field_qoi.cuh", "adjoint.cuh", "mesh_prep.h"]
 
 
 def _nvcc() -> str:

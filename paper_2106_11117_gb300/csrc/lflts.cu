@@ -30,6 +30,7 @@
 #include "kernels.cuh"
 #include "mesh_prep.h"
 #include "moving.cuh"
+#include "restride.cuh"
 
 using namespace lflts;
 
@@ -150,6 +151,7 @@ struct GraphEntry {
 
 struct Workspace {
   Buf ua, ub, d, g, r0, r1, r2, r3, W, xipad, xraw, qps, qpc, Q, uN;
+  Buf cmp;                             // scratch of a ragged batch's stride narrowing
   Buf dts, sig;                        // per-draw dt and (dt / dt_ref)^2 of a ragged batch
   std::vector<double> h_dts;           // host copies of the two (kept for the async copies)
   std::vector<unsigned char> h_sig;
@@ -655,6 +657,9 @@ struct Stepper {
     }
   }
 
+  // Row stride of the arrays after a narrowing copy (S_act unchanged).
+  void set_stride(int64_t S_new) { S = S_new; }
+
   // Narrow the launches to the draws [0, S_new) (a ragged batch whose other
   // draws have reached their own step count).
   void set_active(int64_t S_new) {
@@ -1001,8 +1006,9 @@ struct SliceTask {
 
 template <typename Real>
 struct LoopOut {  // what the loop does with finished draws
-  std::function<int(const Real* u, int64_t s_lo, int64_t s_hi)> qoi_range;
+  std::function<int(const Real* u, int64_t stride, int64_t s_lo, int64_t s_hi)> qoi_range;
   std::function<int()> qoi_final;
+  bool restride = false;  // the loop may narrow the row stride (no state gather)
 };
 
 template <typename Real, int VEC>
@@ -1017,6 +1023,9 @@ struct SlicedLoop : SliceTask {
   std::vector<RaggedSeg> segs;
   size_t active;  // segments 0 .. active-1 still step
   LoopOut<Real> out;
+  Workspace* wsp;
+  int64_t S_cur;   // row stride of the arrays
+  int64_t n_w;     // rows of W
   SlicedLoop(lflts_ctx* c_, const lflts_solve_desc& ds, const MeshGPU& mg, int n_R, int64_t S, Workspace& ws,
              cudaStream_t st_, int cps, const RaggedSpec* rg, LoopOut<Real> o)
       : c(c_),
@@ -1028,7 +1037,10 @@ struct SlicedLoop : SliceTask {
         d(static_cast<Real*>(ws.d.p)),
         N(ds.n_steps),
         st(st_),
-        out(std::move(o)) {
+        out(std::move(o)),
+        wsp(&ws),
+        S_cur(S),
+        n_w(mg.h.n_w) {
     stp.xi_pad = static_cast<const Real*>(ws.xipad.p);
     if (rg) {
       segs = rg->segs;
@@ -1043,11 +1055,39 @@ struct SlicedLoop : SliceTask {
     bool narrowed = false;
     while (active > 0 && segs[active - 1].n_steps <= n) {
       const RaggedSeg& sg = segs[active - 1];
-      LF_TRY(out.qoi_range(uc, sg.off, sg.off + sg.cnt));
+      LF_TRY(out.qoi_range(uc, S_cur, sg.off, sg.off + sg.cnt));
       --active;
       narrowed = true;
     }
-    if (narrowed && active > 0) stp.set_active(segs[active - 1].off + segs[active - 1].cnt);
+    if (narrowed && active > 0) {
+      const int64_t S_act = segs[active - 1].off + segs[active - 1].cnt;
+      stp.set_active(S_act);
+      const int64_t S_new = (S_act + 7) / 8 * 8;  // 32-byte rows at least (one DRAM sector in FP32)
+      if (out.restride && 2 * S_new <= S_cur) LF_TRY(narrow(S_new));
+    }
+    return 0;
+  }
+  // Copy u_n, d and W to rows of stride S_new (through the scratch buffer),
+  // and u_n again into u_next: a step writes u_next only on free nodes, so its
+  // Dirichlet rows must already hold their values at the new stride.  g and
+  // the r buffers are written before they are read again.
+  int narrow(int64_t S_new) {
+    const int64_t n_nodes = stp.mgp->h.n_nodes;
+    Real* tmp = static_cast<Real*>(wsp->cmp.p);
+    auto one = [&](Real* a, int64_t rows) -> int {
+      const int64_t n = rows * S_new;
+      k_restride<Real><<<blocks_for(n, 256, c->sms * 32), 256, 0, st>>>(a, tmp, rows, (int)S_cur, (int)S_new);
+      LF_CUDA(c, cudaGetLastError());
+      c->launches++;
+      LF_CUDA(c, cudaMemcpyAsync(a, tmp, size_t(n) * sizeof(Real), cudaMemcpyDeviceToDevice, st));
+      return 0;
+    };
+    LF_TRY(one(uc, n_nodes));
+    LF_CUDA(c, cudaMemcpyAsync(un, uc, size_t(n_nodes * S_new) * sizeof(Real), cudaMemcpyDeviceToDevice, st));
+    LF_TRY(one(d, n_nodes));
+    LF_TRY(one(static_cast<Real*>(wsp->W.p), std::max<int64_t>(n_w, 1)));
+    S_cur = S_new;
+    stp.set_stride(S_new);
     return 0;
   }
   int advance(int64_t steps) override {
@@ -1306,6 +1346,8 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   LF_TRY(ensure(c, ws.xipad, size_t(S) * KP * rb));
   LF_TRY(ensure(c, ws.qps, size_t(n_chunks) * S * sizeof(double)));
   LF_TRY(ensure(c, ws.qpc, size_t(n_chunks) * S * sizeof(double)));
+  if (rg && rg->segs.size() > 1 && !d_uN)  // a narrowing copy keeps at most half the stride
+    LF_TRY(ensure(c, ws.cmp, size_t(std::max<int64_t>(n_nodes, std::max<int64_t>(h.n_w, 1))) * ((S + 1) / 2 + 8) * rb));
   Real* ua = static_cast<Real*>(ws.ua.p);
   Real* ub = static_cast<Real*>(ws.ub.p);
   Real* d = static_cast<Real*>(ws.d.p);
@@ -1359,13 +1401,20 @@ int run_solve_kp(lflts_ctx* c, const lflts_solve_desc& ds, MeshGPU& mg, const Qo
   const int* new2old = mg.new2old;
   int* d_bad = c->d_bad;
   LoopOut<Real> lo;
-  lo.qoi_range = [=](const Real* uc, int64_t s_lo, int64_t s_hi) -> int {
+  lo.restride = rg && rg->segs.size() > 1 && !d_uN;
+  lo.qoi_range = [=](const Real* uc, int64_t stride, int64_t s_lo, int64_t s_hi) -> int {
     const int64_t w = s_hi - s_lo;
     const int tb = static_cast<int>(std::min<int64_t>(w, 128));
     Prof pr(c, st);
-    k_qoi_partial<Real><<<dim3(n_chunks, static_cast<unsigned>((w + tb - 1) / tb)), tb, 0, st>>>(
-        uc, (int)S, qp->idx, qp->g, qp->nnz, chunk, static_cast<double*>(wsp->qps.p),
-        static_cast<double*>(wsp->qpc.p), (int)s_lo, (int)s_hi);
+    const dim3 qg(n_chunks, static_cast<unsigned>((w + tb - 1) / tb));
+    if (stride == S)
+      k_qoi_partial<Real><<<qg, tb, 0, st>>>(uc, (int)S, qp->idx, qp->g, qp->nnz, chunk,
+                                             static_cast<double*>(wsp->qps.p), static_cast<double*>(wsp->qpc.p),
+                                             (int)s_lo, (int)s_hi);
+    else  // the state's rows narrowed to `stride` (ragged batch)
+      k_qoi_partial_rs<Real><<<qg, tb, 0, st>>>(uc, (int)stride, qp->idx, qp->g, qp->nnz, chunk,
+                                                static_cast<double*>(wsp->qps.p), static_cast<double*>(wsp->qpc.p),
+                                                (int)S, (int)s_lo, (int)s_hi);
     LF_CUDA(c, cudaGetLastError());
     pr.end(LFLTS_KERNEL_QOI, double(qp->nnz) * w * rb);
     if (d_uN) {
@@ -2222,12 +2271,12 @@ int lflts_destroy(lflts_ctx* c) {
       if (w)
         for (auto& ge : w->graphs) cudaGraphExecDestroy(ge.exec);
     for (auto& w : c->ws)
-      for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->r3, &w->W, &w->xipad, &w->xraw, &w->qps,
+      for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->r3, &w->cmp, &w->W, &w->xipad, &w->xraw, &w->qps,
                      &w->qpc, &w->Q, &w->uN, &w->dts, &w->sig})
         if (b->p) cudaFree(b->p);
     for (Workspace* w : {c->gws.get(), c->fws[0].get(), c->fws[1].get()})
       if (w)
-        for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->r3, &w->W, &w->xipad, &w->xraw, &w->qps,
+        for (Buf* b : {&w->ua, &w->ub, &w->d, &w->g, &w->r0, &w->r1, &w->r2, &w->r3, &w->cmp, &w->W, &w->xipad, &w->xraw, &w->qps,
                        &w->qpc, &w->Q, &w->uN, &w->dts, &w->sig})
           if (b->p) cudaFree(b->p);
     if (c->fb)
