@@ -7,7 +7,7 @@ integral of the moved mesh is conserved; and the level pairs of the
 benchmark configuration (60 coarse cells per unit length) agree with the
 oracle's dQ at dQ's own scale.
 
-Tolerances.  FP32: QoI 1e-5 of the batch's QoI scale (the north-star bound;
+Tolerances.  FP32: QoI 1e-5 of the batch's QoI scale (the FP32 bound of the QoI;
 measured 6e-6), state 1e-4.  FP64: with p = 100 substeps the Chebyshev
 recursion of Alg. 2 amplifies rounding about p^2 times more than at p = 8
 (the oracle's z-form and the kernels' increment form differ by 1.7e-11 of
