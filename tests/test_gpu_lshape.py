@@ -22,7 +22,7 @@ def lf():
 
 
 # Relative to the batch's largest |Q| (fine and coarse): FP32 1e-5 (the
-# the FP32 bound of the QoI); FP64 1e-11.  On the graded L-shape the QoI (a box mean
+# required FP32 bound of the QoI); FP64 1e-11.  On the graded L-shape the QoI (a box mean
 # far from the point source) is 10 to 40 times smaller than the state's
 # largest value, and two algebraically equivalent FP64 forms of Alg. 2 (the
 # oracle's z-form on full values and the u-form on increments that the
