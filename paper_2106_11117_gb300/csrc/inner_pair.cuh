@@ -138,8 +138,11 @@ __device__ __forceinline__ Nb4 nb4_of(const int4 a, const int4 b) {
 
 // LAST: the second substep is the step's last one (d, u updated).  Block:
 // 256 threads, SB lanes of VEC draws per row (SB * VEC = 32 draws a slab).
+// Registers capped for five CTAs per SM (48; the kernel is latency-bound,
+// and five CTAs ran the pairs 7 % faster than four, six 60 % slower with
+// the spills a 40-register cap takes).
 template <typename Real, int VEC, bool LAST>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 5)
 k_inner_pair(MeshDev<Real> m, PairDev pd, int S, int SB, const Real* __restrict__ W,
              const Real* __restrict__ cur, Real s_cur, const Real* __restrict__ prev, Real s_prev,
              const Real* __restrict__ g, Real* __restrict__ out1, Real* __restrict__ out2,
