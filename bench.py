@@ -210,11 +210,11 @@ def setup_gpu(cfg, rank, n_slices, autotune=True):
     if not autotune:
         # for a launch list under a profiler (whose serialisation would skew
         # the autotuner's timings): the inner kernels the autotuner picks for
-        # this hierarchy on GB300, paired substeps where |R| >= 500,000
-        # (levels 3 and 4 of square128-p8-K8-L5), default shapes otherwise
+        # this hierarchy on GB300, paired substeps where |R| >= 200,000
+        # (levels 2-4 of square128-p8-K8-L5), default shapes otherwise
         lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_AUTOTUNE, 0)
         lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_PAIRED_INNER, 2)
-        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_PAIR_MIN_R, 500000)
+        lflts.lflts_set_option(ctx.h, lflts.LFLTS_OPT_PAIR_MIN_R, 200000)
     hs = []
     for l in range(cfg.levels):
         lev = level_problem(cfg, l)
@@ -462,8 +462,8 @@ CAPTURED = {
                "dram_bytes": 925.441024e6 + 336.92416e6, "alg_bytes": 12.0 * 1838369 * 32},
     # the second pair launch of a step (profiles/k_inner_pair_square128-L3-S32.md);
     # its traffic also depends on the block plan (mesh_prep.cpp)
-    "inner_pair": {"src": ["kernels.cuh", "inner_pair.cuh", "mesh_prep.cpp"], "sha16": "a9568a36c5373978",
-                   "dram_bytes": 586.460928e6 + 185.795584e6, "alg_bytes": 20.0 * 805987 * 32},
+    "inner_pair": {"src": ["kernels.cuh", "inner_pair.cuh", "mesh_prep.cpp"], "sha16": "f38aa14cabab141a",
+                   "dram_bytes": 635.711232e6 + 193.946368e6, "alg_bytes": 20.0 * 805987 * 32},
 }
 
 
