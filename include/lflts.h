@@ -435,7 +435,7 @@ int lflts_grad_xi(lflts_ctx* ctx, const lflts_solve_desc* desc, const double* xi
  * ceil(nnz / 512) * S <= 131072 partial sums; larger calls return
  * LFLTS_ERR_ARG without launching anything.  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress, with the
- * device current); make that first call before any stream capture.  All
+ * device current) and keeps it for later calls.  All
  * calls on a device share the array and every call overwrites what it
  * reads, so nothing needs clearing, but calls whose kernels overlap on the
  * GPU (different streams, no ordering between them) race on it.  The call
