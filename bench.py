@@ -513,12 +513,14 @@ def _roofline(prof, classes, names):
     """Roofline record of the kernel class with the most device time:
     achieved = algorithmic bytes / time over its launches (the library books
     3 values per free node and coarse launch, 4 per node of R and inner
-    substep, 3 per node of R for a launch of all substeps; per-draw edge
+    substep, 5 per node of R for two substeps in one launch (7 when they end
+    the step), 3 per node of R for a launch of all substeps; per-draw edge
     weights not counted), against the measured HBM copy bandwidth.  traffic:
     DRAM bytes per launch, the captured launch's DRAM/algorithmic ratio times
     this class's algorithmic bytes per launch (traffic grows with the draws
     and nodes a launch covers), null without a capture of the current kernel
-    source."""
+    source; dram_achieved / dram_frac: that traffic over the live launch
+    time, the rate of the bytes the kernel actually moves."""
     peak, peak_kind = _peaks()
     total = sum(v["ms"] for v in prof.values()) or 1.0
     dom = max(classes, key=lambda k: prof[k]["ms"])
@@ -529,9 +531,13 @@ def _roofline(prof, classes, names):
     traffic = None
     if cap and cap["sha16"] == _src_sha16(cap["src"]):
         traffic = cap["dram_bytes"] / cap["alg_bytes"] * per
+    avg_s = pd["ms"] * 1e-3 / max(pd["launches"], 1)
+    dram = traffic / avg_s / 1e9 if traffic and avg_s > 0 else None
     return {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "traffic_over_alg": traffic / per if traffic else None,
+            "dram_achieved": round(dram, 1) if dram else None,
+            "dram_frac": round(dram / peak, 4) if dram else None,
             "alg_bytes_per_launch": per, "launches": pd["launches"],
             "avg_launch_ms": pd["ms"] / max(pd["launches"], 1),
             "share_of_kernel_time": round(pd["ms"] / total, 4)}

@@ -68,10 +68,15 @@ def test_roofline_traffic_from_the_capture_of_the_current_kernels():
     cap = bench.CAPTURED["inner"]
     assert abs(r["traffic"] - cap["dram_bytes"] / cap["alg_bytes"] * 360e9 / 70) < 1.0
     assert 1.0 < r["traffic_over_alg"] < 2.0
+    # the DRAM rate: that traffic over the average launch time (60 ms / 70)
+    assert r["dram_achieved"] == round(r["traffic"] / (0.060 / 70) / 1e9, 1)
+    assert r["dram_frac"] == round(r["dram_achieved"] / r["peak"], 4)
+    assert r["dram_frac"] > r["frac"]
     saved = cap["sha16"]
     try:
         cap["sha16"] = "0" * 16
-        assert bench._roofline(prof, ("coarse", "inner"), names)["traffic"] is None
+        r0 = bench._roofline(prof, ("coarse", "inner"), names)
+        assert r0["traffic"] is None and r0["dram_achieved"] is None and r0["dram_frac"] is None
     finally:
         cap["sha16"] = saved
 
