@@ -1,6 +1,6 @@
 """In-tree build of liblflts.so for sm_103a (nvcc + g++, no cmake).
 
-The two translation units compile in parallel; the CUDA runtime is linked
+The translation units compile in parallel; the CUDA runtime is linked
 statically so the library only needs the driver at run time.
 """
 from __future__ import annotations
